@@ -1,0 +1,512 @@
+#!/usr/bin/env python
+"""Benchmark: load-balanced CSR SpMV forward + backward on GB300.
+
+One step is one pass of the whole hot path over the large power-law matrix
+(m = n = 4,194,304, ~64M nonzeros, Pareto row lengths with exponent 1.3, rows up to 500k):
+
+  forward   y  = A x      lb_spmv: merge-path partition + persistent SpMV + carry fixup
+  backward  dx = A^T g    lb_spmv_t: merge-path over the CSC view (built once, outside timing)
+            dv = g . x    lb_spmv_dvalues: per-nonzero map over the forward partition
+
+``value`` is whole-job algorithmic GB/s: bytes = nnz*(value+index) + offsets + x + y for each
+of the three passes (counting every dense vector once), divided by the device time of the
+timed steps, summed over ranks.  ``--impl reference`` times the FP64 CPU oracle on the same
+workload instead (this project's reference arm).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       (N > 1 under torchrun: independent replicas, one per GPU, weak scaling)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CSR SpMV GB/s as % of GB300 HBM peak; fwd+bwd and batched vs plain"
+UNIT = "GB/s"
+WORKLOAD = "powerlaw_4m"
+FALLBACK_HBM_GBS = 6800.0
+MAIN_KERNEL = "merge_spmv_kernel (plain, FP32 values)"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    p.add_argument("--extras", action="store_true", help="also time batched-vs-plain and BF16-vs-FP32")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------------------------------
+# Algorithmic bytes (the method's minimum traffic; every dense vector counted once).
+
+
+def spmv_bytes(m: int, n: int, nnz: int, value_bytes: int = 4) -> int:
+    return nnz * (value_bytes + 4) + 4 * (m + 1) + 4 * n + 4 * m
+
+
+def dvalues_bytes(m: int, n: int, nnz: int) -> int:
+    # reads col_idx and writes dvalues per nonzero; reads offsets, g and x once.
+    return nnz * (4 + 4) + 4 * (m + 1) + 4 * m + 4 * n
+
+
+def step_bytes(m, n, nnz, value_bytes=4):
+    fwd = spmv_bytes(m, n, nnz, value_bytes)
+    bwd_t = spmv_bytes(n, m, nnz, value_bytes)
+    dv = dvalues_bytes(m, n, nnz)
+    return fwd, bwd_t, dv
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lb_merge.cuh", "lb_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2212_08964_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the main kernel from a committed ncu summary, if the kernel
+    source has not changed since it was captured; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("kernel_source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------------------
+# Clocks during the timed region.
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# Distributed plumbing (one process per GPU; replicas, no data-path collective).
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def _cuda_ok():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (the baseline leg and the reference arm).
+
+
+def oracle_step_time(a, x64, g64, v64, threads=0, budget_s=12.0, max_steps=None):
+    """Mean seconds of one oracle fwd + bwd step (oracle as it stands) over a bounded run."""
+    import oracle
+
+    oracle.build()
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.spmv(a.row_offsets, a.col_idx, v64, x64, threads)
+        oracle.spmv_t(a.row_offsets, a.col_idx, v64, g64, a.n, threads)
+        oracle.dvalues(a.row_offsets, a.col_idx, g64, x64, threads)
+        times.append(time.perf_counter() - t0)
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if max_steps is None and time.perf_counter() - t_start > budget_s:
+            break
+    return float(np.mean(times)), len(times)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------------
+
+
+def make_inputs(workload: str):
+    from paper_2212_08964_gb300 import synth
+
+    a = synth.workload(workload)
+    rng = np.random.default_rng(1234)
+    x = synth.uniform_pm1(rng, a.n)
+    g = synth.uniform_pm1(rng, a.m)
+    return a, x, g
+
+
+def row_sample(a, m_s: int):
+    """The leading m_s rows of a CSR matrix (all columns)."""
+    from paper_2212_08964_gb300 import synth
+
+    m_s = max(1, min(a.m, m_s))
+    nz = int(a.row_offsets[m_s])
+    return synth.CSR(m_s, a.n, a.row_offsets[: m_s + 1].copy(), a.col_idx[:nz], a.values[:nz])
+
+
+def run_reference(args, budget_s: float = 150.0):
+    rank, world, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    a, x, g = make_inputs(args.workload)
+    import oracle
+
+    cores = oracle.max_threads()
+    x64, g64 = x.astype(np.float64), g.astype(np.float64)
+    t_full, _ = oracle_step_time(a, x64, g64, a.values.astype(np.float64), max_steps=1)
+    K, W = max(args.steps, 1), max(args.warmup, 0)
+    per_step = budget_s / (K + W)
+    if t_full <= per_step:
+        s, sample = a, f"full {args.workload} fwd+bwd per step"
+    else:
+        s = row_sample(a, int(a.m * per_step / t_full))
+        sample = f"leading {s.m} of {a.m} rows ({s.nnz} nonzeros) of {args.workload}, fwd+bwd per step"
+    v64 = s.values.astype(np.float64)
+    if W:
+        oracle_step_time(s, x64, g64[: s.m], v64, max_steps=W)
+    sec, steps = oracle_step_time(s, x64, g64[: s.m], v64, max_steps=K)
+    fwd, bwd, dv = step_bytes(s.m, s.n, s.nnz)
+    value = (fwd + bwd + dv) / sec / 1e9
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps, "warmup": W,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded power-law CSR)",
+        "config": {"workload": f"{args.workload} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2212_08964_gb300 import lbspmv as lb
+
+    rank, world, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library is the only compute path)")
+    torch.cuda.set_device(local)
+    lb.ensure_loaded()
+    a, x, g = make_inputs(args.workload)
+    dev = torch.device("cuda", local)
+    ro = torch.from_numpy(a.row_offsets).to(dev)
+    ci = torch.from_numpy(a.col_idx).to(dev)
+    v = torch.from_numpy(a.values).to(dev)
+    xd = torch.from_numpy(x).to(dev)
+    gd = torch.from_numpy(g).to(dev)
+    y = torch.empty(a.m, device=dev)
+    dx = torch.empty(a.n, device=dev)
+    dv = torch.empty(a.nnz, device=dev)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    plan.build_transpose(ci)
+    info = plan.info()
+    torch.cuda.synchronize()
+
+    def step(vals, xx, gg):
+        lb.spmv(ro, ci, vals, xx, out=y)
+        plan.spmv_t(vals, gg, out=dx)
+        plan.dvalues(ci, gg, xx, out=dv)
+
+    launches_per_step = 3 + 2 + 1
+    fwd_b, bwd_b, dv_b = step_bytes(a.m, a.n, a.nnz)
+    total_b = fwd_b + bwd_b + dv_b
+
+    for _ in range(max(args.warmup, 3)):
+        step(v, xd, gd)
+    K = max(args.steps, 1)
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for e in ev_b + ev_a:  # create the events before the timed region
+        e.record()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0.record()
+        for i in range(K):
+            lb.set_profile_events(ev_b[i], ev_a[i])
+            step(v, xd, gd)
+        t1.record()
+        torch.cuda.synchronize()
+    lb.set_profile_events(None, None)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / K
+    ms_max = max_over_ranks(ms, world)
+    main_ms = float(np.mean([b.elapsed_time(e) for b, e in zip(ev_b, ev_a)]))
+    assert lb.device_error() == 0
+
+    peak, peak_kind = measured_hbm_peak()
+    achieved = fwd_b / (main_ms * 1e-3) / 1e9
+    value = total_b * world / (ms_max * 1e-3) / 1e9
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(args.warmup, 3),
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded power-law CSR, uniform[-1,1] values, x and g)",
+        "config": {
+            "workload": f"{args.workload} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz,
+            "schedule": info["schedule"], "threads": info["threads"], "items_per_thread": info["items_per_thread"],
+            "num_tiles": info["num_tiles"], "parallelism": f"replicas x{world}",
+            "l2": f"no flush: each step streams {total_b / 1e9:.2f} GB of inputs, above the 129 MB L2",
+            "bytes_per_step": {"forward": fwd_b, "backward_dx": bwd_b, "backward_dvalues": dv_b},
+        },
+        "roofline": {
+            "bound": "hbm", "kernel": MAIN_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": recorded_traffic(args.workload),
+            "algorithmic_bytes_per_launch": fwd_b, "avg_launch_ms": main_ms,
+        },
+        "gpu_launches": launches_per_step * K,
+        "clocks": clocks.summary(),
+    }
+    result["roofline"]["frac_of"] = f"of {peak_kind}"
+
+    # End to end through the public API with host buffers: per step, H2D of the values, x and
+    # g from pinned memory, then the D2H read of y, dx and dvalues.
+    if not args.no_e2e:
+        h_v = torch.from_numpy(a.values).pin_memory()
+        h_x = torch.from_numpy(x).pin_memory()
+        h_g = torch.from_numpy(g).pin_memory()
+        o_y = torch.empty(a.m, pin_memory=True)
+        o_dx = torch.empty(a.n, pin_memory=True)
+        o_dv = torch.empty(a.nnz, pin_memory=True)
+        d_v, d_x, d_g = torch.empty_like(v), torch.empty_like(xd), torch.empty_like(gd)
+
+        def e2e_step():
+            d_v.copy_(h_v, non_blocking=True)
+            d_x.copy_(h_x, non_blocking=True)
+            d_g.copy_(h_g, non_blocking=True)
+            step(d_v, d_x, d_g)
+            o_y.copy_(y, non_blocking=True)
+            o_dx.copy_(dx, non_blocking=True)
+            o_dv.copy_(dv, non_blocking=True)
+
+        Ke = max(1, min(K, 50))
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(Ke):
+            e2e_step()
+        s1.record()
+        torch.cuda.synchronize()
+        barrier(world)
+        e_ms = max_over_ranks(s0.elapsed_time(s1) / Ke, world)
+        h2d = (a.values.nbytes + x.nbytes + g.nbytes)
+        d2h = 4 * (a.m + a.n + a.nnz)
+        result["e2e"] = {"value": total_b * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke}
+
+    if args.extras and rank == 0:
+        result["extras"] = run_extras(lb, torch, dev)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        cores = oracle.max_threads()
+        sec, steps = oracle_step_time(a, x.astype(np.float64), g.astype(np.float64), a.values.astype(np.float64))
+        result["cpu_baseline"] = {"value": total_b / sec / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": f"{steps} full fwd+bwd steps of {args.workload} (FP64 C oracle, OpenMP)"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def run_extras(lb, torch, dev):
+    """Batched vs per-matrix plain calls, and BF16/FP16 values vs FP32 values."""
+    from paper_2212_08964_gb300 import synth
+
+    out = {}
+    # BF16 / FP16 vs FP32 values on the 8M-row power-law matrix (forward only).
+    a = synth.workload("powerlaw_8m")
+    x = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(6), a.n)).to(dev)
+    ro, ci = torch.from_numpy(a.row_offsets).to(dev), torch.from_numpy(a.col_idx).to(dev)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    y = torch.empty(a.m, device=dev)
+    for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
+        v = torch.from_numpy(a.values).to(dev).to(dt)
+        ms = _time(torch, lambda: plan.spmv(ci, v, x, out=y), 20)
+        out[f"powerlaw_8m_{name}"] = {"ms": ms, "GB/s": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9}
+    del plan, v, ci, ro
+    # Batched (one launch, CUDA graph) vs one planned call per matrix.
+    b = synth.workload("batched_4096")
+    xs = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(5), int(b.ns.sum()))).to(dev)
+    bci, bv = torch.from_numpy(b.col_idx).to(dev), torch.from_numpy(b.values).to(dev)
+    bro = torch.from_numpy(b.row_offsets).to(dev)
+    bp = lb.BatchedPlan(b.ms, b.ns, b.nnzs, bro)
+    yb = torch.empty(int(b.ms.sum()), device=dev)
+    bp.spmv(bci, bv, xs, out=yb)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bp.spmv(bci, bv, xs, out=yb)
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(graph):
+        bp.spmv(bci, bv, xs, out=yb)
+    ms_b = _time(torch, graph.replay, 20)
+    total = sum(spmv_bytes(int(m), int(n), int(z)) for m, n, z in zip(b.ms, b.ns, b.nnzs))
+    out["batched_4096_graph"] = {"ms": ms_b, "GB/s": total / (ms_b * 1e-3) / 1e9, "launches": 2}
+    # Per-matrix plans, one call each.
+    plans, views = [], []
+    ro_pos = nz_pos = x_pos = y_pos = 0
+    for i in range(b.count):
+        m, n, z = int(b.ms[i]), int(b.ns[i]), int(b.nnzs[i])
+        p = lb.Plan(bro[ro_pos: ro_pos + m + 1], n, z, schedule="merge_path")
+        plans.append(p)
+        views.append((bci[nz_pos: nz_pos + z], bv[nz_pos: nz_pos + z], xs[x_pos: x_pos + n], yb[y_pos: y_pos + m]))
+        ro_pos += m + 1
+        nz_pos += z
+        x_pos += n
+        y_pos += m
+
+    def per_matrix():
+        for p, (c_, v_, x_, y_) in zip(plans, views):
+            p.spmv(c_, v_, x_, out=y_)
+
+    ms_p = _time(torch, per_matrix, 3)
+    out["batched_4096_per_matrix_calls"] = {"ms": ms_p, "GB/s": total / (ms_p * 1e-3) / 1e9, "launches": 2 * b.count}
+    out["batched_speedup_vs_per_matrix"] = ms_p / ms_b
+    return out
+
+
+def _time(torch, fn, reps):
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

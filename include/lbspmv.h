@@ -1,0 +1,224 @@
+/*
+ * lbspmv.h -- load-balanced CSR sparse matrix-vector multiply for NVIDIA GB300 (sm_103a).
+ *
+ * The method is the atom/tile/tile-set load-balancing model of "GPU Load Balancing"
+ * (M. Osama, 2022): a work atom is a nonzero, a work tile is a row, the tile set is the
+ * matrix (Ch.3 Sec. "Terminology"; Ch.4 Sec. "Input from Sparse Data Structures").  SpMV
+ * runs under one of three schedule families:
+ *   - thread-mapped: one row per thread (Ch.3 Sec. "Thread-Mapped"; Listing lst:spmv);
+ *   - group-mapped: a group of threads (4..32 lanes, a warp, or a block) per set of rows,
+ *     with a prefix sum of row lengths and a binary search atom -> row (Ch.3 Sec.
+ *     "Group-Mapped", Alg. alg:group-mapped; Ch.4 Sec. "Group-level load balancing");
+ *   - merge-path (work-oriented): rows + nonzeros split evenly, a 2-D diagonal search per
+ *     split, partial rows carried out and fixed up afterwards (Ch.3 Sec. "Work-Oriented",
+ *     Alg. alg:work-oriented; Ch.4 Sec. "Merge-path load balancing").
+ *
+ * Conventions for every call below.
+ *   - All array arguments are DEVICE pointers owned by the caller unless a parameter says
+ *     "host".  The library never frees caller memory.  Any alignment is accepted.
+ *   - Indices are int32: row_offsets[m+1] (row_offsets[0] == 0, non-decreasing,
+ *     row_offsets[m] == nnz), col_idx[nnz] in [0, n).  Values are FP32, BF16 or FP16
+ *     (lb_dtype); x, y, g, dx and dvalues are FP32; accumulation is FP32.
+ *   - y is OVERWRITTEN: y = A x (no beta).  Empty rows give 0.  m == 0 is a no-op;
+ *     nnz == 0 gives y = 0.
+ *   - Work is stream-ordered on `stream` (0 = the legacy default stream).  No call
+ *     synchronizes the device except the ones documented as copying results to the host.
+ *     lb_spmv_planned, lb_spmv_t, lb_spmv_dvalues and lb_spmv_batched allocate nothing and
+ *     never synchronize.
+ *   - Argument errors are reported before any GPU work as LB_ERR_INVALID_ARG; CUDA errors
+ *     as LB_ERR_CUDA.  Kernels never trap: a kernel that gives up on a bounded wait
+ *     records LB_ERR_TIMEOUT in a device error word read by lb_device_error().
+ *   - Matrix contents are not checked by the SpMV calls; lb_validate_csr checks them.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef LBSPMV_H
+#define LBSPMV_H
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID_ARG = -1, /* bad size, null pointer, unknown enum, plan of the wrong kind */
+    LB_ERR_BAD_MATRIX = -2,  /* malformed matrix contents (found by a check or a kernel) */
+    LB_ERR_UNSUPPORTED = -3, /* valid request this build does not implement */
+    LB_ERR_NO_MEMORY = -4,   /* a plan or workspace allocation failed */
+    LB_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+    LB_ERR_TIMEOUT = -6      /* a kernel gave up on a bounded wait (device error word) */
+} lb_status;
+
+typedef enum {
+    LB_SCHED_AUTO = 0,          /* merge-path unless (min(m, n) < 500 and nnz < 10000) */
+    LB_SCHED_THREAD_MAPPED = 1, /* Ch.3 Sec. "Thread-Mapped"; Listing lst:thread-mapped */
+    LB_SCHED_WARP_MAPPED = 2,   /* group-mapped with a 32-lane group (Ch.4 "Warp- and block-level") */
+    LB_SCHED_BLOCK_MAPPED = 3,  /* group-mapped with the whole block as the group */
+    LB_SCHED_GROUP_MAPPED = 4,  /* group-mapped, group_size in {4, 8, 16, 32} */
+    LB_SCHED_MERGE_PATH = 5     /* work-oriented merge-path (Alg. alg:work-oriented) */
+} lb_schedule;
+
+typedef enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 } lb_dtype;
+
+/* Launch shape of a schedule; 0 selects the default.
+ *   merge-path:   (threads, items_per_thread) in {(128, 8), (256, 4), (256, 8), (256, 12),
+ *                 (256, 16), (512, 8)}, default (256, 8); one tile holds
+ *                 threads * items_per_thread work items (rows + nonzeros);
+ *   block-mapped: threads in {128, 256} (the group is the block);
+ *   group-mapped: group_size in {4, 8, 16, 32}. */
+typedef struct {
+    int threads;
+    int items_per_thread;
+    int group_size;
+} lb_tuning;
+
+typedef struct lb_plan lb_plan;
+typedef struct lb_batched_plan lb_batched_plan;
+
+/* Human-readable name of a status code (static storage). */
+const char *lb_status_string(lb_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int lb_version(void);
+
+/*
+ * y = A x for a CSR matrix, in one call: the dissertation's kernel signature
+ * spmv(rows, cols, nnz, offsets, indices, values, x, y) (Listing lst:spmv) plus a value
+ * type and a stream.  The schedule is chosen by the rule of Ch.4 Sec. "Improved Performance
+ * Response" (merge-path unless min(m, n) < 500 and nnz < 10000; then group- or thread-mapped
+ * by the mean row length).  Merge-path recomputes its partition every call and takes its
+ * workspace with cudaMallocAsync / cudaFreeAsync on `stream`.
+ */
+lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_idx,
+                  const void *values, lb_dtype vdt, const float *x, float *y, cudaStream_t stream);
+
+/*
+ * Merge-path partition (Alg. alg:work-oriented, "2DSearch"; Ch.4 Sec. "Merge-path load
+ * balancing").  Row ends R_r (key row_offsets[r+1]) are merged with nonzero indices N_k
+ * (key k), R_r before N_k when row_offsets[r+1] <= k.  For tile boundaries
+ * d_c = min(c * tile_items, m + nnz), c = 0..G with G = ceil((m + nnz) / tile_items), writes
+ * tile_row[c] = #{r : r + row_offsets[r+1] < d_c} (row ends before d_c) and
+ * tile_nz[c] = d_c - tile_row[c] (nonzeros before d_c).  tile_row and tile_nz are device
+ * arrays of G + 1 ints.  Bit-exact; no allocation.
+ */
+lb_status lb_partition(int m, int nnz, const int *row_offsets, int tile_items, int *tile_row,
+                       int *tile_nz, cudaStream_t stream);
+
+/* Number of tiles G for lb_partition (host arithmetic only). */
+int lb_num_tiles(int m, int nnz, int tile_items);
+
+/*
+ * Build a plan for one sparsity structure.  The plan copies row_offsets (device, m + 1
+ * ints), resolves LB_SCHED_AUTO, and for merge-path computes the partition once and owns
+ * the carry buffers, so lb_spmv_planned allocates nothing.  `t` may be NULL.  The work is
+ * enqueued on `stream`; the plan is usable on any stream ordered after it.
+ */
+lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_schedule s,
+                         const lb_tuning *t, cudaStream_t stream, lb_plan **out);
+
+/* Resolved schedule and launch shape of a plan; any output pointer may be NULL. */
+lb_status lb_plan_info(const lb_plan *p, lb_schedule *s, lb_tuning *t, int *num_tiles,
+                       int *tile_items);
+
+/*
+ * Copy a plan's merge-path partition to HOST arrays of num_tiles + 1 ints (synchronizes
+ * the device).  transposed = 0: the forward (CSR) partition; 1: the CSC partition built by
+ * lb_plan_build_transpose.  With tile_row == NULL only *num_tiles is written.
+ */
+lb_status lb_plan_partition(const lb_plan *p, int transposed, int *tile_row, int *tile_nz,
+                            int *num_tiles);
+
+/* y = A x with a plan (no allocation, no synchronization; CUDA-graph capturable). */
+lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
+                          const float *x, float *y, cudaStream_t stream);
+
+/*
+ * Build the CSC view of the plan's matrix, once (after checking offsets and column range as
+ * lb_validate_csr does; LB_ERR_BAD_MATRIX if they fail): col_offsets[n+1], row_idx[nnz] and
+ * perm[nnz] (perm[p] = the CSR index of CSC entry p) by a stable transpose (entries of a
+ * column keep increasing CSR index), plus the merge-path partition of the transposed
+ * matrix.  The framework's atom/tile view covers CSC as it covers CSR (Ch.4 Sec.
+ * "Implementing Sparse Data Structures"; "Merge-path load balancing": any format with an
+ * atoms-per-tile count).  Deterministic; allocates plan memory and temporary workspace.
+ */
+lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t stream);
+
+/* Copy the CSC view to HOST arrays (n + 1, nnz, nnz ints); synchronizes the device. */
+lb_status lb_plan_transpose(const lb_plan *p, int *col_offsets, int *row_idx, int *perm);
+
+/*
+ * dx = A^T g (backward of y = A x with respect to x): merge-path SpMV over the CSC view,
+ * tiles = columns, atoms = CSC entries, values read in CSR order through perm.  Requires
+ * lb_plan_build_transpose.  g: m floats, dx: n floats (overwritten).
+ */
+lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
+                    cudaStream_t stream);
+
+/*
+ * dvalues[k] = g[row(k)] * x[col_idx[k]] (backward of y = A x with respect to the values),
+ * one coalesced pass over the nonzeros; row(k) comes from the plan's merge-path partition
+ * (each tile stages its row ends and searches them).  Merge-path plans only.
+ */
+lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x,
+                          float *dvalues, cudaStream_t stream);
+
+void lb_plan_destroy(lb_plan *p);
+
+/*
+ * Plan for `count` independent CSR matrices run as one block-diagonal matrix (the
+ * "sets of sets" extension of Ch.6 Sec. "Multi-GPU Load Balancing": merge-path keeps its
+ * structure one level up).  h_m, h_n, h_nnz: HOST arrays of `count` sizes.
+ * row_offsets_concat (device) concatenates each matrix's own offsets (m_i + 1 entries,
+ * each starting at 0).  The plan materializes the block-diagonal row offsets and one
+ * global merge-path partition over sum(m_i + nnz_i).  s must be LB_SCHED_AUTO or
+ * LB_SCHED_MERGE_PATH.
+ */
+lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, const int *h_nnz,
+                                 const int *row_offsets_concat, lb_schedule s, const lb_tuning *t,
+                                 cudaStream_t stream, lb_batched_plan **out);
+
+/* Copy the global partition to HOST arrays of num_tiles + 1 ints (synchronizes). */
+lb_status lb_batched_plan_partition(const lb_batched_plan *p, int *tile_row, int *tile_nz,
+                                    int *num_tiles);
+
+/*
+ * y_i = A_i x_i for every matrix of the plan in ONE persistent launch plus the fixup.
+ * col_idx_concat holds local column indices; values_concat, x_concat (sum n_i floats) and
+ * y_concat (sum m_i floats) are concatenated in matrix order.  No allocation.
+ */
+lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat,
+                          const void *values_concat, lb_dtype vdt, const float *x_concat,
+                          float *y_concat, cudaStream_t stream);
+
+void lb_batched_plan_destroy(lb_batched_plan *p);
+
+/*
+ * Check a CSR matrix on the device and write a bit mask to the device int *d_status
+ * (0 = valid): 1 row_offsets[0] != 0; 2 row_offsets decreasing somewhere; 4
+ * row_offsets[m] != nnz; 8 a column index outside [0, n); 16 (only with check_sorted)
+ * columns of a row not strictly increasing.  Never traps.
+ */
+lb_status lb_validate_csr(int m, int n, int nnz, const int *row_offsets, const int *col_idx,
+                          int check_sorted, int *d_status, cudaStream_t stream);
+
+/*
+ * Read the current device's error word into *status; clear it when `clear` is nonzero.
+ * Synchronizes the device.  LB_OK, or the last error a kernel recorded: LB_ERR_TIMEOUT (a
+ * bounded wait gave up) or LB_ERR_BAD_MATRIX (a merge-path tile held more work than a tile
+ * can, which only malformed row offsets produce; that tile was skipped).
+ */
+lb_status lb_device_error(int *status, int clear);
+
+/*
+ * Profiling aid: while set (non-NULL), every merge-path SpMV call records `before` right
+ * before and `after` right after its main kernel on the call's stream.  Process-wide, not
+ * thread-safe; pass NULLs to stop.
+ */
+lb_status lb_set_profile_events(cudaEvent_t before, cudaEvent_t after);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBSPMV_H */

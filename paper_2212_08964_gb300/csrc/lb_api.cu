@@ -1,0 +1,659 @@
+// lb_api.cu -- the C ABI of liblbspmv (declared in include/lbspmv.h).
+//
+// Host-side only: argument checks, plan objects, schedule selection and kernel dispatch.
+// Every step of the computation runs in this library's kernels.
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "lb_internal.cuh"
+
+using namespace lb;
+
+// Device error word (per device; kernels that give up on a bounded wait write here).
+__device__ int g_lb_device_error = 0;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kDefaultThreads = 256;
+constexpr int kDefaultIpt = 8;
+
+cudaEvent_t g_ev_before = nullptr;
+cudaEvent_t g_ev_after = nullptr;
+
+int *device_error_word() {
+    static int *ptrs[kMaxDevices] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (ptrs[dev]) return ptrs[dev];
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_lb_device_error) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<int *>(p);
+    }
+    return ptrs[dev];
+}
+
+bool merge_shape_ok(int threads, int ipt) {
+    static const int shapes[][2] = {{128, 8}, {256, 4}, {256, 8}, {256, 12}, {256, 16}, {512, 8}};
+    for (const auto &s : shapes)
+        if (s[0] == threads && s[1] == ipt) return true;
+    return false;
+}
+
+bool dtype_ok(lb_dtype d) { return d == LB_F32 || d == LB_BF16 || d == LB_F16; }
+
+bool sched_ok(lb_schedule s) { return s >= LB_SCHED_AUTO && s <= LB_SCHED_MERGE_PATH; }
+
+// Resolve a requested schedule and tuning into concrete values, or report an invalid request.
+bool resolve(int m, int n, int nnz, lb_schedule s, const lb_tuning *t, lb_schedule *out_s, lb_tuning *out_t) {
+    lb_tuning r = t ? *t : lb_tuning{0, 0, 0};
+    if (s == LB_SCHED_AUTO) {
+        // Ch.4 Sec. "Improved Performance Response": merge-path unless rows or columns are below
+        // alpha = 500 and the nonzeros below beta = 10000; then thread- or group-mapped.  The
+        // paper leaves the choice between those two open; short rows go to thread-mapped, longer
+        // ones to the smallest group covering the mean row length.
+        const long long mn = m < n ? m : n;
+        if (mn < 500 && nnz < 10000) {
+            const double mean = m > 0 ? static_cast<double>(nnz) / m : 0.0;
+            if (mean <= 4.0) {
+                s = LB_SCHED_THREAD_MAPPED;
+            } else {
+                int g = 4;
+                while (g < 32 && g < mean) g <<= 1;
+                s = LB_SCHED_GROUP_MAPPED;
+                r.group_size = g;
+            }
+        } else {
+            s = LB_SCHED_MERGE_PATH;
+        }
+    }
+    switch (s) {
+        case LB_SCHED_MERGE_PATH:
+            if (r.threads == 0) r.threads = kDefaultThreads;
+            if (r.items_per_thread == 0) r.items_per_thread = kDefaultIpt;
+            if (!merge_shape_ok(r.threads, r.items_per_thread)) return false;
+            break;
+        case LB_SCHED_THREAD_MAPPED:
+            break;
+        case LB_SCHED_WARP_MAPPED:
+            r.group_size = 32;
+            break;
+        case LB_SCHED_BLOCK_MAPPED:
+            if (r.threads == 0) r.threads = 256;
+            if (r.threads != 128 && r.threads != 256) return false;
+            break;
+        case LB_SCHED_GROUP_MAPPED:
+            if (r.group_size == 0) r.group_size = 32;
+            if (r.group_size != 4 && r.group_size != 8 && r.group_size != 16 && r.group_size != 32) return false;
+            break;
+        default:
+            return false;
+    }
+    *out_s = s;
+    *out_t = r;
+    return true;
+}
+
+lb_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return LB_OK;
+    if (e == cudaErrorMemoryAllocation) return LB_ERR_NO_MEMORY;
+    return LB_ERR_CUDA;
+}
+
+bool sizes_ok(int m, int n, int nnz) {
+    if (m < 0 || n < 0 || nnz < 0) return false;
+    if (m == 0 && nnz != 0) return false;
+    if (n == 0 && nnz != 0) return false;
+    return true;
+}
+
+int num_tiles_of(long long m, long long nnz, int tile_items) {
+    const long long W = m + nnz;
+    return static_cast<int>((W + tile_items - 1) / tile_items);
+}
+
+template <typename P>
+cudaError_t dmalloc(P **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P));
+}
+
+}  // namespace
+
+struct lb_plan {
+    int device = -1;
+    int m = 0, n = 0, nnz = 0;
+    lb_schedule sched = LB_SCHED_MERGE_PATH;
+    lb_tuning tune = {0, 0, 0};
+    int tile_items = 0;
+    int G = 0;
+    int *ro = nullptr;
+    int *tile_row = nullptr, *tile_nz = nullptr, *carry_row = nullptr;
+    float *carry_val = nullptr;
+    bool has_t = false;
+    int Gt = 0;
+    int *co = nullptr, *ri = nullptr, *perm = nullptr;
+    int *t_tile_row = nullptr, *t_tile_nz = nullptr, *t_carry_row = nullptr;
+    float *t_carry_val = nullptr;
+};
+
+struct lb_batched_plan {
+    int device = -1;
+    int count = 0, kc = 0;
+    long long total_rows = 0, total_cols = 0, total_nnz = 0;
+    lb_tuning tune = {0, 0, 0};
+    int tile_items = 0;
+    int G = 0;
+    int *ro_g = nullptr, *mat_nz_base = nullptr, *mat_col_base = nullptr;
+    int *tile_row = nullptr, *tile_nz = nullptr, *tile_mat = nullptr, *carry_row = nullptr;
+    float *carry_val = nullptr;
+};
+
+static void free_plan_arrays(lb_plan *p) {
+    int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row, p->co, p->ri, p->perm, p->t_tile_row,
+                   p->t_tile_nz, p->t_carry_row};
+    for (int *q : ints)
+        if (q) cudaFree(q);
+    if (p->carry_val) cudaFree(p->carry_val);
+    if (p->t_carry_val) cudaFree(p->t_carry_val);
+}
+
+static void release_transpose(lb_plan *p) {
+    int **ints[] = {&p->co, &p->ri, &p->perm, &p->t_tile_row, &p->t_tile_nz, &p->t_carry_row};
+    for (int **q : ints) {
+        if (*q) cudaFree(*q);
+        *q = nullptr;
+    }
+    if (p->t_carry_val) cudaFree(p->t_carry_val);
+    p->t_carry_val = nullptr;
+}
+
+static bool on_device(int dev) {
+    int cur = -1;
+    return cudaGetDevice(&cur) == cudaSuccess && cur == dev;
+}
+
+extern "C" {
+
+const char *lb_status_string(lb_status s) {
+    switch (s) {
+        case LB_OK:
+            return "LB_OK";
+        case LB_ERR_INVALID_ARG:
+            return "LB_ERR_INVALID_ARG: invalid argument";
+        case LB_ERR_BAD_MATRIX:
+            return "LB_ERR_BAD_MATRIX: malformed matrix";
+        case LB_ERR_UNSUPPORTED:
+            return "LB_ERR_UNSUPPORTED: not supported by this build";
+        case LB_ERR_NO_MEMORY:
+            return "LB_ERR_NO_MEMORY: device allocation failed";
+        case LB_ERR_CUDA:
+            return "LB_ERR_CUDA: CUDA runtime error";
+        case LB_ERR_TIMEOUT:
+            return "LB_ERR_TIMEOUT: a kernel gave up on a bounded wait";
+    }
+    return "unknown lb_status";
+}
+
+int lb_version(void) { return 10000; }
+
+int lb_num_tiles(int m, int nnz, int tile_items) {
+    if (m < 0 || nnz < 0 || tile_items <= 0) return -1;
+    return num_tiles_of(m, nnz, tile_items);
+}
+
+lb_status lb_set_profile_events(cudaEvent_t before, cudaEvent_t after) {
+    g_ev_before = before;
+    g_ev_after = after;
+    return LB_OK;
+}
+
+lb_status lb_partition(int m, int nnz, const int *row_offsets, int tile_items, int *tile_row, int *tile_nz,
+                       cudaStream_t stream) {
+    if (m < 0 || nnz < 0 || tile_items <= 0 || (m == 0 && nnz != 0)) return LB_ERR_INVALID_ARG;
+    if (!row_offsets || !tile_row || !tile_nz) return LB_ERR_INVALID_ARG;
+    return from_cuda(launch_partition(m, nnz, row_offsets, tile_items, tile_row, tile_nz, stream));
+}
+
+lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_idx, const void *values,
+                  lb_dtype vdt, const float *x, float *y, cudaStream_t stream) {
+    if (!sizes_ok(m, n, nnz) || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
+    if (m == 0) return LB_OK;
+    if (!row_offsets || !y) return LB_ERR_INVALID_ARG;
+    if (nnz > 0 && (!col_idx || !values || !x)) return LB_ERR_INVALID_ARG;
+    if (nnz == 0) return from_cuda(cudaMemsetAsync(y, 0, static_cast<size_t>(m) * sizeof(float), stream));
+    lb_schedule s;
+    lb_tuning t;
+    if (!resolve(m, n, nnz, LB_SCHED_AUTO, nullptr, &s, &t)) return LB_ERR_INVALID_ARG;
+    if (s != LB_SCHED_MERGE_PATH) return from_cuda(launch_mapped(s, t, vdt, m, row_offsets, col_idx, values, x, y, stream));
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    const int T = t.threads * t.items_per_thread;
+    const int G = num_tiles_of(m, nnz, T);
+    // Workspace: tile_row[G+1], tile_nz[G+1], carry_row[G], carry_val[G].
+    const size_t bytes = (2 * (static_cast<size_t>(G) + 1) + static_cast<size_t>(G)) * sizeof(int) +
+                         static_cast<size_t>(G) * sizeof(float);
+    void *ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, bytes, stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    int *tile_row = static_cast<int *>(ws);
+    int *tile_nz = tile_row + G + 1;
+    int *carry_row = tile_nz + G + 1;
+    float *carry_val = reinterpret_cast<float *>(carry_row + G);
+    e = launch_partition(m, nnz, row_offsets, T, tile_row, tile_nz, stream);
+    if (e == cudaSuccess) {
+        MergeArgs a{};
+        a.num_tiles = G;
+        a.num_rows = m;
+        a.tile_row = tile_row;
+        a.tile_nz = tile_nz;
+        a.row_end = row_offsets + 1;
+        a.idx = col_idx;
+        a.val = values;
+        a.x = x;
+        a.y = y;
+        a.carry_row = carry_row;
+        a.carry_val = carry_val;
+        a.err = err;
+        e = launch_merge_spmv(vdt, kPlain, t.threads, t.items_per_thread, a, stream, g_ev_before, g_ev_after);
+    }
+    cudaError_t e2 = cudaFreeAsync(ws, stream);
+    return from_cuda(e != cudaSuccess ? e : e2);
+}
+
+lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_schedule s, const lb_tuning *t,
+                         cudaStream_t stream, lb_plan **out) {
+    if (!out) return LB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!sizes_ok(m, n, nnz) || !sched_ok(s)) return LB_ERR_INVALID_ARG;
+    if (!row_offsets && m > 0) return LB_ERR_INVALID_ARG;
+    lb_plan *p = new (std::nothrow) lb_plan();
+    if (!p) return LB_ERR_NO_MEMORY;
+    if (!resolve(m, n, nnz, s, t, &p->sched, &p->tune)) {
+        delete p;
+        return LB_ERR_INVALID_ARG;
+    }
+    cudaGetDevice(&p->device);
+    p->m = m;
+    p->n = n;
+    p->nnz = nnz;
+    // The forward partition is built for every schedule (dvalues and the transpose use it).
+    const int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
+    const int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
+    p->tile_items = threads * ipt;
+    p->G = num_tiles_of(m, nnz, p->tile_items);
+    cudaError_t e = cudaSuccess;
+    if ((e = dmalloc(&p->ro, static_cast<size_t>(m) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->tile_row, static_cast<size_t>(p->G) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->tile_nz, static_cast<size_t>(p->G) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->carry_row, static_cast<size_t>(p->G))) != cudaSuccess ||
+        (e = dmalloc(&p->carry_val, static_cast<size_t>(p->G))) != cudaSuccess) {
+        free_plan_arrays(p);
+        delete p;
+        return from_cuda(e);
+    }
+    if (m > 0) {
+        e = cudaMemcpyAsync(p->ro, row_offsets, (static_cast<size_t>(m) + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
+                            stream);
+        if (e == cudaSuccess) e = launch_partition(m, nnz, p->ro, p->tile_items, p->tile_row, p->tile_nz, stream);
+    } else {
+        int zero[2] = {0, 0};
+        e = cudaMemcpy(p->ro, zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->tile_row, zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->tile_nz, zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        free_plan_arrays(p);
+        delete p;
+        return from_cuda(e);
+    }
+    *out = p;
+    return LB_OK;
+}
+
+lb_status lb_plan_info(const lb_plan *p, lb_schedule *s, lb_tuning *t, int *num_tiles, int *tile_items) {
+    if (!p) return LB_ERR_INVALID_ARG;
+    if (s) *s = p->sched;
+    if (t) *t = p->tune;
+    if (num_tiles) *num_tiles = p->G;
+    if (tile_items) *tile_items = p->tile_items;
+    return LB_OK;
+}
+
+lb_status lb_plan_partition(const lb_plan *p, int transposed, int *tile_row, int *tile_nz, int *num_tiles) {
+    if (!p || !num_tiles) return LB_ERR_INVALID_ARG;
+    if (transposed && !p->has_t) return LB_ERR_INVALID_ARG;
+    const int G = transposed ? p->Gt : p->G;
+    *num_tiles = G;
+    if (!tile_row) return LB_OK;
+    if (!tile_nz) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    const size_t bytes = (static_cast<size_t>(G) + 1) * sizeof(int);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(tile_row, transposed ? p->t_tile_row : p->tile_row, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tile_nz, transposed ? p->t_tile_nz : p->tile_nz, bytes, cudaMemcpyDeviceToHost);
+    return from_cuda(e);
+}
+
+lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, const float *x,
+                          float *y, cudaStream_t stream) {
+    if (!p || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
+    if (p->m == 0) return LB_OK;
+    if (!y || (p->nnz > 0 && (!col_idx || !values || !x))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(y, 0, static_cast<size_t>(p->m) * sizeof(float), stream));
+    if (p->sched != LB_SCHED_MERGE_PATH)
+        return from_cuda(launch_mapped(p->sched, p->tune, vdt, p->m, p->ro, col_idx, values, x, y, stream));
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    MergeArgs a{};
+    a.num_tiles = p->G;
+    a.num_rows = p->m;
+    a.tile_row = p->tile_row;
+    a.tile_nz = p->tile_nz;
+    a.row_end = p->ro + 1;
+    a.idx = col_idx;
+    a.val = values;
+    a.x = x;
+    a.y = y;
+    a.carry_row = p->carry_row;
+    a.carry_val = p->carry_val;
+    a.err = err;
+    return from_cuda(launch_merge_spmv(vdt, kPlain, p->tune.threads, p->tune.items_per_thread, a, stream, g_ev_before,
+                                       g_ev_after));
+}
+
+lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t stream) {
+    if (!p) return LB_ERR_INVALID_ARG;
+    if (p->nnz > 0 && !col_idx) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->has_t) return LB_OK;
+    const int n = p->n, nnz = p->nnz;
+    cudaError_t e = cudaSuccess;
+    // The counting pass indexes by column, so the structure is checked first (one sync; the
+    // transpose is built once per structure).
+    {
+        int *d_status = nullptr, h_status = 0;
+        if ((e = cudaMallocAsync(reinterpret_cast<void **>(&d_status), sizeof(int), stream)) != cudaSuccess)
+            return from_cuda(e);
+        e = launch_validate(p->m, n, nnz, p->ro, col_idx, 0, d_status, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        cudaFreeAsync(d_status, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        if (h_status != 0) return LB_ERR_BAD_MATRIX;
+    }
+    p->Gt = num_tiles_of(n, nnz, p->tile_items);
+    if ((e = dmalloc(&p->co, static_cast<size_t>(n) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->ri, static_cast<size_t>(nnz))) != cudaSuccess ||
+        (e = dmalloc(&p->perm, static_cast<size_t>(nnz))) != cudaSuccess ||
+        (e = dmalloc(&p->t_tile_row, static_cast<size_t>(p->Gt) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->t_tile_nz, static_cast<size_t>(p->Gt) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->t_carry_row, static_cast<size_t>(p->Gt))) != cudaSuccess ||
+        (e = dmalloc(&p->t_carry_val, static_cast<size_t>(p->Gt))) != cudaSuccess) {
+        release_transpose(p);
+        return from_cuda(e);
+    }
+    TransposeOut out{p->co, p->ri, p->perm};
+    e = build_transpose(p->m, n, nnz, p->ro, col_idx, p->G, p->tile_items, p->tile_row, p->tile_nz, out, stream);
+    if (e == cudaSuccess) {
+        if (n > 0) {
+            e = launch_partition(n, nnz, p->co, p->tile_items, p->t_tile_row, p->t_tile_nz, stream);
+        } else {
+            e = cudaMemsetAsync(p->t_tile_row, 0, sizeof(int), stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->t_tile_nz, 0, sizeof(int), stream);
+        }
+    }
+    if (e != cudaSuccess) {
+        release_transpose(p);
+        return from_cuda(e);
+    }
+    p->has_t = true;
+    return LB_OK;
+}
+
+lb_status lb_plan_transpose(const lb_plan *p, int *col_offsets, int *row_idx, int *perm) {
+    if (!p || !p->has_t || !col_offsets || (p->nnz > 0 && (!row_idx || !perm))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(col_offsets, p->co, (static_cast<size_t>(p->n) + 1) * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && p->nnz > 0)
+        e = cudaMemcpy(row_idx, p->ri, static_cast<size_t>(p->nnz) * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && p->nnz > 0)
+        e = cudaMemcpy(perm, p->perm, static_cast<size_t>(p->nnz) * sizeof(int), cudaMemcpyDeviceToHost);
+    return from_cuda(e);
+}
+
+lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
+                    cudaStream_t stream) {
+    if (!p || !p->has_t || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
+    if (p->n == 0) return LB_OK;
+    if (!dx || (p->nnz > 0 && (!values || !g))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream));
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    MergeArgs a{};
+    a.num_tiles = p->Gt;
+    a.num_rows = p->n;
+    a.tile_row = p->t_tile_row;
+    a.tile_nz = p->t_tile_nz;
+    a.row_end = p->co + 1;
+    a.idx = p->ri;
+    a.val = values;
+    a.perm = p->perm;
+    a.x = g;
+    a.y = dx;
+    a.carry_row = p->t_carry_row;
+    a.carry_val = p->t_carry_val;
+    a.err = err;
+    const int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
+    const int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
+    return from_cuda(launch_merge_spmv(vdt, kTransposed, threads, ipt, a, stream, nullptr, nullptr));
+}
+
+lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
+                          cudaStream_t stream) {
+    if (!p) return LB_ERR_INVALID_ARG;
+    if (p->nnz == 0) return LB_OK;
+    if (!col_idx || !g || !x || !dvalues) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    return from_cuda(
+        launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, dvalues, stream));
+}
+
+void lb_plan_destroy(lb_plan *p) {
+    if (!p) return;
+    free_plan_arrays(p);
+    delete p;
+}
+
+lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, const int *h_nnz,
+                                 const int *row_offsets_concat, lb_schedule s, const lb_tuning *t,
+                                 cudaStream_t stream, lb_batched_plan **out) {
+    if (!out) return LB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 0 || (count > 0 && (!h_m || !h_n || !h_nnz))) return LB_ERR_INVALID_ARG;
+    if (s != LB_SCHED_AUTO && s != LB_SCHED_MERGE_PATH) return LB_ERR_UNSUPPORTED;
+    lb_tuning r = t ? *t : lb_tuning{0, 0, 0};
+    if (r.threads == 0) r.threads = kDefaultThreads;
+    if (r.items_per_thread == 0) r.items_per_thread = kDefaultIpt;
+    if (!merge_shape_ok(r.threads, r.items_per_thread)) return LB_ERR_INVALID_ARG;
+    // Host bases over the non-empty matrices.
+    std::vector<int> ro_pos, row_base(1, 0), nz_base(1, 0), col_base;
+    long long rows = 0, cols = 0, nnz = 0, pos = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!sizes_ok(h_m[i], h_n[i], h_nnz[i])) return LB_ERR_INVALID_ARG;
+        if (h_m[i] > 0) {
+            ro_pos.push_back(static_cast<int>(pos));
+            rows += h_m[i];
+            nnz += h_nnz[i];
+            if (rows >= INT_MAX || nnz >= INT_MAX || pos >= INT_MAX) return LB_ERR_INVALID_ARG;
+            row_base.push_back(static_cast<int>(rows));
+            nz_base.push_back(static_cast<int>(nnz));
+            col_base.push_back(static_cast<int>(cols));
+        }
+        pos += static_cast<long long>(h_m[i]) + 1;
+        cols += h_n[i];
+        if (cols >= INT_MAX) return LB_ERR_INVALID_ARG;
+    }
+    if (rows > 0 && !row_offsets_concat) return LB_ERR_INVALID_ARG;
+    lb_batched_plan *p = new (std::nothrow) lb_batched_plan();
+    if (!p) return LB_ERR_NO_MEMORY;
+    cudaGetDevice(&p->device);
+    p->count = count;
+    p->kc = static_cast<int>(ro_pos.size());
+    p->total_rows = rows;
+    p->total_cols = cols;
+    p->total_nnz = nnz;
+    p->tune = r;
+    p->tile_items = r.threads * r.items_per_thread;
+    p->G = num_tiles_of(rows, nnz, p->tile_items);
+    const int kc = p->kc;
+    int *d_ro_pos = nullptr, *d_row_base = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t err) {
+        if (d_ro_pos) cudaFree(d_ro_pos);
+        if (d_row_base) cudaFree(d_row_base);
+        lb_batched_plan_destroy(p);
+        return from_cuda(err);
+    };
+    if ((e = dmalloc(&p->ro_g, static_cast<size_t>(rows) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->mat_nz_base, static_cast<size_t>(kc) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->mat_col_base, static_cast<size_t>(kc) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->tile_row, static_cast<size_t>(p->G) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->tile_nz, static_cast<size_t>(p->G) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->tile_mat, static_cast<size_t>(p->G) + 1)) != cudaSuccess ||
+        (e = dmalloc(&p->carry_row, static_cast<size_t>(p->G))) != cudaSuccess ||
+        (e = dmalloc(&p->carry_val, static_cast<size_t>(p->G))) != cudaSuccess ||
+        (e = dmalloc(&d_ro_pos, static_cast<size_t>(kc) + 1)) != cudaSuccess ||
+        (e = dmalloc(&d_row_base, static_cast<size_t>(kc) + 1)) != cudaSuccess)
+        return fail(e);
+    if (kc == 0) {
+        const int zero = 0;
+        e = cudaMemcpy(p->ro_g, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->tile_row, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->tile_nz, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->tile_mat, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(e);
+        cudaFree(d_ro_pos);
+        cudaFree(d_row_base);
+        *out = p;
+        return LB_OK;
+    }
+    // Synchronous copies: the host vectors die at return.
+    if ((e = cudaMemcpy(d_ro_pos, ro_pos.data(), kc * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d_row_base, row_base.data(), (kc + 1) * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->mat_nz_base, nz_base.data(), (kc + 1) * sizeof(int), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(p->mat_col_base, col_base.data(), kc * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    e = launch_block_diag_offsets(kc, d_ro_pos, d_row_base, p->mat_nz_base, row_offsets_concat,
+                                  static_cast<int>(rows), p->ro_g, stream);
+    if (e == cudaSuccess)
+        e = launch_partition(static_cast<int>(rows), nnz, p->ro_g, p->tile_items, p->tile_row, p->tile_nz, stream);
+    if (e == cudaSuccess) e = launch_tile_matrix(p->G, p->tile_nz, kc, p->mat_nz_base, p->tile_mat, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the index scratch is freed below
+    if (e != cudaSuccess) return fail(e);
+    cudaFree(d_ro_pos);
+    cudaFree(d_row_base);
+    *out = p;
+    return LB_OK;
+}
+
+lb_status lb_batched_plan_partition(const lb_batched_plan *p, int *tile_row, int *tile_nz, int *num_tiles) {
+    if (!p || !num_tiles) return LB_ERR_INVALID_ARG;
+    *num_tiles = p->G;
+    if (!tile_row) return LB_OK;
+    if (!tile_nz || !on_device(p->device)) return LB_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    const size_t bytes = (static_cast<size_t>(p->G) + 1) * sizeof(int);
+    if (e == cudaSuccess) e = cudaMemcpy(tile_row, p->tile_row, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tile_nz, p->tile_nz, bytes, cudaMemcpyDeviceToHost);
+    return from_cuda(e);
+}
+
+lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, const void *values_concat,
+                          lb_dtype vdt, const float *x_concat, float *y_concat, cudaStream_t stream) {
+    if (!p || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
+    if (p->total_rows == 0) return LB_OK;
+    if (!y_concat || (p->total_nnz > 0 && (!col_idx_concat || !values_concat || !x_concat)))
+        return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->total_nnz == 0)
+        return from_cuda(cudaMemsetAsync(y_concat, 0, static_cast<size_t>(p->total_rows) * sizeof(float), stream));
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    MergeArgs a{};
+    a.num_tiles = p->G;
+    a.num_rows = static_cast<int>(p->total_rows);
+    a.tile_row = p->tile_row;
+    a.tile_nz = p->tile_nz;
+    a.row_end = p->ro_g + 1;
+    a.idx = col_idx_concat;
+    a.val = values_concat;
+    a.x = x_concat;
+    a.y = y_concat;
+    a.carry_row = p->carry_row;
+    a.carry_val = p->carry_val;
+    a.mat_nz_base = p->mat_nz_base;
+    a.mat_col_base = p->mat_col_base;
+    a.tile_mat = p->tile_mat;
+    a.err = err;
+    return from_cuda(launch_merge_spmv(vdt, kBatched, p->tune.threads, p->tune.items_per_thread, a, stream,
+                                       g_ev_before, g_ev_after));
+}
+
+void lb_batched_plan_destroy(lb_batched_plan *p) {
+    if (!p) return;
+    int *ints[] = {p->ro_g, p->mat_nz_base, p->mat_col_base, p->tile_row, p->tile_nz, p->tile_mat, p->carry_row};
+    for (int *q : ints)
+        if (q) cudaFree(q);
+    if (p->carry_val) cudaFree(p->carry_val);
+    delete p;
+}
+
+lb_status lb_validate_csr(int m, int n, int nnz, const int *row_offsets, const int *col_idx, int check_sorted,
+                          int *d_status, cudaStream_t stream) {
+    if (!sizes_ok(m, n, nnz) || !d_status || !row_offsets || (nnz > 0 && !col_idx)) return LB_ERR_INVALID_ARG;
+    return from_cuda(launch_validate(m, n, nnz, row_offsets, col_idx, check_sorted, d_status, stream));
+}
+
+lb_status lb_device_error(int *status, int clear) {
+    if (!status) return LB_ERR_INVALID_ARG;
+    int *w = device_error_word();
+    if (!w) return LB_ERR_CUDA;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, w, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(w, 0, sizeof(int));
+    return from_cuda(e);
+}
+
+}  // extern "C"
+
+namespace lb {
+
+cudaError_t launch_merge_spmv(lb_dtype vdt, int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t stream,
+                              cudaEvent_t ev_before, cudaEvent_t ev_after) {
+    switch (vdt) {
+        case LB_F32:
+            return launch_merge_f32(mode, threads, ipt, a, stream, ev_before, ev_after);
+        case LB_BF16:
+            return launch_merge_bf16(mode, threads, ipt, a, stream, ev_before, ev_after);
+        case LB_F16:
+            return launch_merge_f16(mode, threads, ipt, a, stream, ev_before, ev_after);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lb

@@ -1,0 +1,200 @@
+// lb_internal.cuh -- shared device helpers and launcher declarations for liblbspmv.
+//
+// Everything here is GB300-specific (sm_103a): 1-D bulk TMA copies (cp.async.bulk) tracked by
+// shared-memory mbarriers, L2 cache-policy hints, and bounded waits that record an error
+// instead of spinning forever.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbspmv.h"
+
+namespace lb {
+
+// ------------------------------------------------------------------------------------------
+// Value types: stored as FP32, BF16 or FP16, always widened to FP32 in registers.
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+// Neumaier's compensated addition: s + c carries the running sum with an error bound that
+// does not grow with the number of terms.
+__device__ __forceinline__ void kbn_add(float &s, float &c, float v) {
+    float t = s + v;
+    if (fabsf(s) >= fabsf(v))
+        c += (s - t) + v;
+    else
+        c += (v - t) + s;
+    s = t;
+}
+
+// ------------------------------------------------------------------------------------------
+// PTX wrappers.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for an mbarrier phase, giving up after `limit_ns` nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// L2 eviction-priority policies for cache hints.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 1-D bulk copy global -> shared, completion counted on `bar` (both addresses 16-byte aligned,
+// bytes a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                         uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy (TMA)
+// accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Read-only gather with an L2 eviction-priority hint.
+__device__ __forceinline__ float ldg_hint(const float *p, uint64_t policy) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
+// Bounded waits give up after this long (the kernel then records LB_ERR_TIMEOUT).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// ------------------------------------------------------------------------------------------
+// Kernel argument blocks.
+
+// Merge-path SpMV over one tile set.  "Rows" are the tiles of the set (CSR rows, or CSC
+// columns for the transposed product) and "atoms" its nonzeros.
+struct MergeArgs {
+    int num_tiles;        // G
+    int num_rows;         // rows of the set (y has this many entries)
+    const int *tile_row;  // [G+1] row ends consumed before each tile boundary
+    const int *tile_nz;   // [G+1] atoms consumed before each tile boundary
+    const int *row_end;   // row_end[r] = offset one past the last atom of row r (offsets + 1)
+    const int *idx;       // gather index per atom (column index; CSC row index when transposed)
+    const void *val;      // values: per atom, or per CSR nonzero when transposed
+    const int *perm;      // transposed only: CSR nonzero index of each atom
+    const float *x;       // gathered dense vector
+    float *y;             // output, one entry per row
+    int *carry_row;       // [G] row left open at the end of each tile
+    float *carry_val;     // [G] that row's partial sum inside the tile
+    const int *mat_nz_base;   // batched: [K+1] first nonzero of each matrix
+    const int *mat_col_base;  // batched: [K] offset of each matrix's x inside x_concat
+    const int *tile_mat;      // batched: [G+1] matrix holding each tile's first nonzero
+    int *err;                 // device error word
+};
+
+enum MergeMode { kPlain = 0, kBatched = 1, kTransposed = 2 };
+
+// Launch the persistent merge-path kernel followed by the fixup kernel.  `grid` <= 0 picks
+// one wave of resident CTAs.  `ev_before` / `ev_after` (may be null) are recorded around the
+// main kernel.
+cudaError_t launch_merge_spmv(lb_dtype vdt, int mode, int threads, int ipt, const MergeArgs &a,
+                              cudaStream_t stream, cudaEvent_t ev_before, cudaEvent_t ev_after);
+cudaError_t launch_merge_f32(int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t s,
+                             cudaEvent_t eb, cudaEvent_t ea);
+cudaError_t launch_merge_bf16(int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t s,
+                              cudaEvent_t eb, cudaEvent_t ea);
+cudaError_t launch_merge_f16(int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t s,
+                             cudaEvent_t eb, cudaEvent_t ea);
+
+// Fixup: y[r] += sum of the carries of row r, for every carry row r < num_rows.
+cudaError_t launch_fixup(int num_tiles, int num_rows, const int *carry_row, const float *carry_val,
+                         float *y, cudaStream_t stream);
+
+// Merge-path partition of `offsets` (m + 1 entries) into tiles of tile_items work items.
+cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_items, int *tile_row,
+                             int *tile_nz, cudaStream_t stream);
+
+// Thread-, group- and block-mapped schedules.
+cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, const int *ro,
+                          const int *ci, const void *v, const float *x, float *y, cudaStream_t stream);
+
+// dvalues over the forward partition.
+cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
+                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
+                           cudaStream_t stream);
+
+// Stable CSR -> CSC transpose (deterministic LSD radix sort by column).
+struct TransposeOut {
+    int *col_offsets;  // [n+1]
+    int *row_idx;      // [nnz]
+    int *perm;         // [nnz]
+};
+cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci, int num_tiles,
+                            int tile_items, const int *tile_row, const int *tile_nz, TransposeOut out,
+                            cudaStream_t stream);
+
+// Batched-plan helpers.
+cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *row_base, const int *nz_base,
+                                      const int *ro_concat, int total_rows, int *ro_global, cudaStream_t stream);
+cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, const int *mat_nz_base,
+                               int *tile_mat, cudaStream_t stream);
+
+cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
+                            int *d_status, cudaStream_t stream);
+
+// Device properties of the current device (cached).
+int current_sm_count();
+
+}  // namespace lb

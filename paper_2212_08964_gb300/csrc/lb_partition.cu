@@ -1,0 +1,252 @@
+// lb_partition.cu -- merge-path partition, carry fixup, batched-plan helpers, validation.
+#include <mutex>
+
+#include "lb_internal.cuh"
+
+namespace lb {
+
+int current_sm_count() {
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+    if (cache[dev] == 0) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = sms > 0 ? sms : 1;
+    }
+    return cache[dev];
+}
+
+// ------------------------------------------------------------------------------------------
+// Merge-path partition (Alg. alg:work-oriented, the "2DSearch" for every tile boundary).
+//
+// Row end R_r sits at merge position K_r = r + offsets[r+1] (R_r precedes nonzero k exactly
+// when offsets[r+1] <= k), and K_r increases strictly with r.  A boundary d has
+// i(d) = #{r : K_r < d} row ends before it, so i(d) = r exactly for K_{r-1} < d <= K_r
+// (K_{-1} = -1, K_m = W).  Instead of one binary search per boundary, every row r computes
+// the boundaries c with d_c = min(c T, W) in that interval and writes (r, d_c - r) for them:
+// one coalesced pass over the offsets, the same result bit for bit.  A warp shares the
+// writes of its 32 rows, so a row spanning many tiles does not serialize one thread.
+__global__ void __launch_bounds__(256) partition_kernel(int m, long long W, int T, long long G, const int *offsets,
+                                                        int *tile_row, int *tile_nz) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    for (long long base = ((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; base <= m;
+         base += warps * 32) {
+        const long long r = base + lane;
+        long long c_lo = 0, n_c = 0;
+        if (r <= m) {
+            const long long k_prev = (r == 0) ? -1 : (r - 1) + static_cast<long long>(__ldg(offsets + r));
+            const long long k_cur = (r == m) ? W : r + static_cast<long long>(__ldg(offsets + r + 1));
+            c_lo = k_prev + 1 > 0 ? (k_prev + 1 + T - 1) / T : 0;
+            long long c_hi = (r == m) ? G : k_cur / T;
+            if (c_hi > G) c_hi = G;  // only malformed offsets get here; keep writes in [0, G]
+            n_c = c_hi >= c_lo ? c_hi - c_lo + 1 : 0;
+        }
+        // Exclusive prefix of the per-lane boundary counts.
+        long long incl = n_c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        const long long total = __shfl_sync(0xffffffffu, incl, 31);
+        const long long excl = incl - n_c;
+        for (long long q0 = 0; q0 < total; q0 += 32) {  // warp-uniform trip count
+            const long long q = q0 + lane;
+            // Owner: the last lane whose exclusive prefix is <= q.
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi + 1) >> 1;
+                const long long e_mid = __shfl_sync(0xffffffffu, excl, mid);
+                if (e_mid <= q)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const long long e_own = __shfl_sync(0xffffffffu, excl, lo);
+            const long long c_own = __shfl_sync(0xffffffffu, c_lo, lo);
+            if (q >= total) continue;
+            const long long c = c_own + (q - e_own);
+            const long long row = base + lo;
+            const long long d = c * T < W ? c * T : W;
+            tile_row[c] = static_cast<int>(row);
+            tile_nz[c] = static_cast<int>(d - row);
+        }
+    }
+}
+
+cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_items, int *tile_row, int *tile_nz,
+                             cudaStream_t stream) {
+    const long long W = static_cast<long long>(m) + nnz;
+    const long long G = (W + tile_items - 1) / tile_items;
+    const long long threads_needed = (static_cast<long long>(m) + 1 + 31) / 32 * 32;
+    long long blocks = (threads_needed + 255) / 256;
+    const long long cap = static_cast<long long>(current_sm_count()) * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    partition_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(m, W, tile_items, G, offsets, tile_row, tile_nz);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Fixup ("Fix-up" procedure of Alg. alg:work-oriented): y[r] += the carries of row r.
+//
+// Carry rows are non-decreasing in tile order, so the carries of a row form one run.  A warp
+// takes each run start, finds the run's end with 32-way parallel probes, sums the run with
+// compensated per-lane sums and a fixed shuffle tree, and adds the total to y once: a fixed
+// order, so the result is deterministic, and no atomics.
+__global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *carry_row, const float *carry_val,
+                                                    float *y) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    for (long long c = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; c < G; c += warps) {
+        const int r = __ldg(carry_row + c);
+        if (r >= m) continue;
+        if (c > 0 && __ldg(carry_row + c - 1) == r) continue;
+        // Galloping: lane l probes c + 2^l.
+        const long long probe = c + (1ll << lane);
+        const bool in_run = probe < G && __ldg(carry_row + probe) == r;
+        const unsigned run_mask = __ballot_sync(0xffffffffu, in_run);
+        const int L = __popc(run_mask);  // probes 1, 2, .., 2^(L-1) are inside the run
+        long long lo = L == 0 ? c : c + (1ll << (L - 1));
+        long long hi = c + (1ll << L);
+        if (hi > G) hi = G;
+        while (hi - lo > 1) {
+            const long long step = (hi - lo + 31) / 32;
+            const long long q = lo + (lane + 1) * step;
+            const bool in = q < hi && __ldg(carry_row + q) == r;
+            const int cnt = __popc(__ballot_sync(0xffffffffu, in));
+            const long long new_lo = lo + cnt * step;
+            long long new_hi = new_lo + step;
+            if (new_hi > hi) new_hi = hi;
+            lo = new_lo;
+            hi = new_hi;
+        }
+        const long long end = hi;  // carries [c, end) belong to row r
+        float s = 0.f, comp = 0.f;
+        for (long long q = c + lane; q < end; q += 32) kbn_add(s, comp, __ldg(carry_val + q));
+        float v = s + comp;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) y[r] += v;
+    }
+}
+
+cudaError_t launch_fixup(int num_tiles, int num_rows, const int *carry_row, const float *carry_val, float *y,
+                         cudaStream_t stream) {
+    if (num_tiles <= 0) return cudaSuccess;
+    long long blocks = (static_cast<long long>(num_tiles) + 7) / 8;
+    const long long cap = static_cast<long long>(current_sm_count()) * 8;
+    if (blocks > cap) blocks = cap;
+    fixup_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(num_tiles, num_rows, carry_row, carry_val, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched plans: the block-diagonal matrix diag(A_0, .., A_{K-1}) (Ch.6 Sec. "Multi-GPU Load
+// Balancing": merge-path keeps its structure one level up, a "set of sets").
+
+// ro_global[0] = 0; for row r of matrix i, ro_global[row_base[i] + r + 1] =
+// nz_base[i] + ro_concat[ro_pos[i] + r + 1].  One block per matrix, threads over its rows.
+__global__ void __launch_bounds__(256) block_diag_offsets_kernel(int count, const int *ro_pos, const int *row_base,
+                                                                 const int *nz_base, const int *ro_concat,
+                                                                 int *ro_global) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ro_global[0] = 0;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int rb = row_base[i], m_i = row_base[i + 1] - rb, nb = nz_base[i];
+        const int *src = ro_concat + ro_pos[i] + 1;
+        for (int r = threadIdx.x; r < m_i; r += blockDim.x) ro_global[rb + r + 1] = nb + src[r];
+    }
+}
+
+cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *row_base, const int *nz_base,
+                                      const int *ro_concat, int total_rows, int *ro_global, cudaStream_t stream) {
+    (void)total_rows;
+    int blocks = count < current_sm_count() * 8 ? count : current_sm_count() * 8;
+    if (blocks < 1) blocks = 1;
+    block_diag_offsets_kernel<<<blocks, 256, 0, stream>>>(count, ro_pos, row_base, nz_base, ro_concat, ro_global);
+    return cudaGetLastError();
+}
+
+// tile_mat[c] = the matrix holding nonzero tile_nz[c]: the last i with mat_nz_base[i] <= k,
+// clamped to [0, count - 1].
+__global__ void tile_matrix_kernel(int G, const int *tile_nz, int count, const int *mat_nz_base, int *tile_mat) {
+    for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c <= G;
+         c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int k = tile_nz[c];
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (mat_nz_base[mid] <= k)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        tile_mat[c] = lo;
+    }
+}
+
+cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, const int *mat_nz_base, int *tile_mat,
+                               cudaStream_t stream) {
+    const long long n = static_cast<long long>(num_tiles) + 1;
+    int blocks = static_cast<int>((n + 255) / 256);
+    if (blocks > current_sm_count() * 8) blocks = current_sm_count() * 8;
+    tile_matrix_kernel<<<blocks, 256, 0, stream>>>(num_tiles, tile_nz, count, mat_nz_base, tile_mat);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// CSR validation: ORs problem bits into *status (never traps).
+__global__ void validate_offsets_kernel(int m, int nnz, const int *ro, int *status) {
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r <= m;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int bits = 0;
+        const int v = ro[r];
+        if (r == 0 && v != 0) bits |= 1;
+        if (r < m && ro[r + 1] < v) bits |= 2;
+        if (r == m && v != nnz) bits |= 4;
+        if (bits) atomicOr(status, bits);
+    }
+}
+
+// Column checks need row boundaries, which are only trustworthy when the offsets passed; the
+// kernel reads each row's range clamped to [0, nnz] so a broken offsets array cannot send it
+// out of bounds.
+__global__ void validate_columns_kernel(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
+                                        int *status) {
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < m;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        long long b = ro[r], e = ro[r + 1];
+        b = b < 0 ? 0 : (b > nnz ? nnz : b);
+        e = e < b ? b : (e > nnz ? nnz : e);
+        int bits = 0, prev = -1;
+        for (long long k = b; k < e; ++k) {
+            const int c = ci[k];
+            if (c < 0 || c >= n) bits |= 8;
+            if (check_sorted && k > b && c <= prev) bits |= 16;
+            prev = c;
+        }
+        if (bits) atomicOr(status, bits);
+    }
+}
+
+cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted, int *d_status,
+                            cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    int blocks = static_cast<int>((static_cast<long long>(m) + 1 + 255) / 256);
+    if (blocks > current_sm_count() * 16) blocks = current_sm_count() * 16;
+    if (blocks < 1) blocks = 1;
+    validate_offsets_kernel<<<blocks, 256, 0, stream>>>(m, nnz, ro, d_status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (m > 0 && nnz > 0) {
+        validate_columns_kernel<<<blocks, 256, 0, stream>>>(m, n, nnz, ro, ci, check_sorted, d_status);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace lb

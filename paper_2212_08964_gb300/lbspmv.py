@@ -1,0 +1,412 @@
+"""Python binding of liblbspmv (include/lbspmv.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  PyTorch supplies device memory and
+the current stream.  There is no CPU fallback: if the library cannot be built or loaded,
+every call raises.
+
+Names follow the C ABI: ``spmv`` (one call, Listing lst:spmv's signature), ``partition``
+(the merge-path split, Alg. alg:work-oriented), ``Plan`` (a sparsity structure with its
+partition and optional CSC view), ``BatchedPlan`` (many matrices as one block-diagonal
+tile set) and ``SpMV`` (a ``torch.autograd.Function`` whose backward runs A^T g over the CSC
+view and g[row] * x[col] per nonzero).
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+import torch
+
+from . import _build
+
+__all__ = [
+    "LbError",
+    "ensure_loaded",
+    "library_path",
+    "spmv",
+    "partition",
+    "num_tiles",
+    "Plan",
+    "BatchedPlan",
+    "SpMV",
+    "spmv_autograd",
+    "validate_csr",
+    "device_error",
+    "set_profile_events",
+    "SCHEDULES",
+    "MERGE_SHAPES",
+]
+
+LB_OK = 0
+LB_ERR_INVALID_ARG = -1
+LB_ERR_UNSUPPORTED = -3
+LB_ERR_TIMEOUT = -6
+
+SCHEDULES = {
+    "auto": 0,
+    "thread_mapped": 1,
+    "warp_mapped": 2,
+    "block_mapped": 3,
+    "group_mapped": 4,
+    "merge_path": 5,
+}
+_SCHED_NAMES = {v: k for k, v in SCHEDULES.items()}
+# (threads, items per thread) shapes of the merge-path kernel compiled into the library.
+MERGE_SHAPES = [(128, 8), (256, 4), (256, 8), (256, 12), (256, 16), (512, 8)]
+
+_DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+
+
+class LbError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = _lib.lb_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg}")
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("items_per_thread", ctypes.c_int), ("group_size", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def _declare(lib):
+    lib.lb_status_string.restype = ctypes.c_char_p
+    lib.lb_status_string.argtypes = [_I]
+    lib.lb_version.restype = _I
+    sigs = {
+        "lb_spmv": [_I, _I, _I, _P, _P, _P, _I, _P, _P, _P],
+        "lb_partition": [_I, _I, _P, _I, _P, _P, _P],
+        "lb_plan_create": [_I, _I, _I, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
+        "lb_plan_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+        "lb_plan_partition": [_P, _I, _P, _P, ctypes.POINTER(_I)],
+        "lb_spmv_planned": [_P, _P, _P, _I, _P, _P, _P],
+        "lb_plan_build_transpose": [_P, _P, _P],
+        "lb_plan_transpose": [_P, _P, _P, _P],
+        "lb_spmv_t": [_P, _P, _I, _P, _P, _P],
+        "lb_spmv_dvalues": [_P, _P, _P, _P, _P, _P],
+        "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
+        "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
+        "lb_spmv_batched": [_P, _P, _P, _I, _P, _P, _P],
+        "lb_validate_csr": [_I, _I, _I, _P, _P, _I, _P, _P],
+        "lb_device_error": [ctypes.POINTER(_I), _I],
+        "lb_set_profile_events": [_P, _P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = _I
+    lib.lb_num_tiles.argtypes = [_I, _I, _I]
+    lib.lb_num_tiles.restype = _I
+    lib.lb_plan_destroy.argtypes = [_P]
+    lib.lb_plan_destroy.restype = None
+    lib.lb_batched_plan_destroy.argtypes = [_P]
+    lib.lb_batched_plan_destroy.restype = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def ensure_loaded():
+    """Build (if stale) and load liblbspmv.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != LB_OK:
+        raise LbError(status, what)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _need(t: torch.Tensor, dtype, name: str, numel: int | None = None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+
+
+def _vdt(values: torch.Tensor) -> int:
+    try:
+        return _DTYPES[values.dtype]
+    except KeyError:
+        raise TypeError(f"values must be float32, bfloat16 or float16, got {values.dtype}") from None
+
+
+def _tuning(threads=0, items_per_thread=0, group_size=0):
+    return _Tuning(int(threads), int(items_per_thread), int(group_size))
+
+
+def num_tiles(m: int, nnz: int, tile_items: int) -> int:
+    return int(ensure_loaded().lb_num_tiles(m, nnz, tile_items))
+
+
+def spmv(row_offsets, col_idx, values, x, n: int | None = None, out=None, stream=None) -> torch.Tensor:
+    """y = A x in one call (lb_spmv); the schedule follows the alpha/beta rule."""
+    lib = ensure_loaded()
+    m = row_offsets.numel() - 1
+    nnz = col_idx.numel()
+    n = x.numel() if n is None else n
+    _need(row_offsets, torch.int32, "row_offsets")
+    _need(col_idx, torch.int32, "col_idx")
+    _need(values, None, "values", nnz)
+    _need(x, torch.float32, "x", n)
+    y = torch.empty(m, dtype=torch.float32, device=x.device) if out is None else out
+    _need(y, torch.float32, "y", m)
+    _check(
+        lib.lb_spmv(m, n, nnz, _ptr(row_offsets), _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y), _stream(stream)),
+        "lb_spmv",
+    )
+    return y
+
+
+def partition(row_offsets, nnz: int, tile_items: int, stream=None):
+    """Merge-path tile boundaries as two int32 device tensors of G + 1 entries."""
+    lib = ensure_loaded()
+    m = row_offsets.numel() - 1
+    _need(row_offsets, torch.int32, "row_offsets")
+    G = num_tiles(m, nnz, tile_items)
+    tr = torch.empty(G + 1, dtype=torch.int32, device=row_offsets.device)
+    tn = torch.empty(G + 1, dtype=torch.int32, device=row_offsets.device)
+    _check(lib.lb_partition(m, nnz, _ptr(row_offsets), tile_items, _ptr(tr), _ptr(tn), _stream(stream)), "lb_partition")
+    return tr, tn
+
+
+class Plan:
+    """A sparsity structure prepared once: schedule, partition, carries, optional CSC view."""
+
+    def __init__(self, row_offsets: torch.Tensor, n: int, nnz: int | None = None, schedule: str = "auto",
+                 threads: int = 0, items_per_thread: int = 0, group_size: int = 0, stream=None):
+        lib = ensure_loaded()
+        _need(row_offsets, torch.int32, "row_offsets")
+        self.m = row_offsets.numel() - 1
+        self.n = int(n)
+        self.nnz = int(row_offsets[-1].item()) if nnz is None else int(nnz)
+        self.device = row_offsets.device
+        self._h = _P()
+        t = _tuning(threads, items_per_thread, group_size)
+        _check(
+            lib.lb_plan_create(self.m, self.n, self.nnz, _ptr(row_offsets), SCHEDULES[schedule], ctypes.byref(t),
+                               _stream(stream), ctypes.byref(self._h)),
+            "lb_plan_create",
+        )
+        self._has_t = False
+
+    # -- introspection
+    def info(self) -> dict:
+        s, t, g, ti = _I(), _Tuning(), _I(), _I()
+        _check(_lib.lb_plan_info(self._h, ctypes.byref(s), ctypes.byref(t), ctypes.byref(g), ctypes.byref(ti)), "lb_plan_info")
+        return {
+            "schedule": _SCHED_NAMES[s.value],
+            "threads": t.threads,
+            "items_per_thread": t.items_per_thread,
+            "group_size": t.group_size,
+            "num_tiles": g.value,
+            "tile_items": ti.value,
+        }
+
+    def partition(self, transposed: bool = False):
+        g = _I()
+        _check(_lib.lb_plan_partition(self._h, int(transposed), None, None, ctypes.byref(g)), "lb_plan_partition")
+        tr = np.empty(g.value + 1, np.int32)
+        tn = np.empty(g.value + 1, np.int32)
+        _check(_lib.lb_plan_partition(self._h, int(transposed), tr.ctypes.data, tn.ctypes.data, ctypes.byref(g)), "lb_plan_partition")
+        return tr, tn
+
+    # -- forward
+    def spmv(self, col_idx, values, x, out=None, stream=None) -> torch.Tensor:
+        _need(col_idx, torch.int32, "col_idx", self.nnz)
+        _need(values, None, "values", self.nnz)
+        _need(x, torch.float32, "x", self.n)
+        y = torch.empty(self.m, dtype=torch.float32, device=x.device) if out is None else out
+        _need(y, torch.float32, "y", self.m)
+        _check(_lib.lb_spmv_planned(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y), _stream(stream)),
+               "lb_spmv_planned")
+        return y
+
+    # -- backward
+    def build_transpose(self, col_idx, stream=None):
+        _need(col_idx, torch.int32, "col_idx", self.nnz)
+        _check(_lib.lb_plan_build_transpose(self._h, _ptr(col_idx), _stream(stream)), "lb_plan_build_transpose")
+        self._has_t = True
+
+    @property
+    def has_transpose(self) -> bool:
+        return self._has_t
+
+    def transpose(self):
+        co = np.empty(self.n + 1, np.int32)
+        ri = np.empty(max(self.nnz, 1), np.int32)
+        perm = np.empty(max(self.nnz, 1), np.int32)
+        _check(_lib.lb_plan_transpose(self._h, co.ctypes.data, ri.ctypes.data, perm.ctypes.data), "lb_plan_transpose")
+        return co, ri[: self.nnz], perm[: self.nnz]
+
+    def spmv_t(self, values, g, out=None, stream=None) -> torch.Tensor:
+        _need(values, None, "values", self.nnz)
+        _need(g, torch.float32, "g", self.m)
+        dx = torch.empty(self.n, dtype=torch.float32, device=g.device) if out is None else out
+        _need(dx, torch.float32, "dx", self.n)
+        _check(_lib.lb_spmv_t(self._h, _ptr(values), _vdt(values), _ptr(g), _ptr(dx), _stream(stream)), "lb_spmv_t")
+        return dx
+
+    def dvalues(self, col_idx, g, x, out=None, stream=None) -> torch.Tensor:
+        _need(col_idx, torch.int32, "col_idx", self.nnz)
+        _need(g, torch.float32, "g", self.m)
+        _need(x, torch.float32, "x", self.n)
+        dv = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if out is None else out
+        _need(dv, torch.float32, "dvalues", self.nnz)
+        _check(_lib.lb_spmv_dvalues(self._h, _ptr(col_idx), _ptr(g), _ptr(x), _ptr(dv), _stream(stream)), "lb_spmv_dvalues")
+        return dv
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.lb_plan_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchedPlan:
+    """K CSR matrices run as one block-diagonal matrix in one persistent launch."""
+
+    def __init__(self, ms, ns, nnzs, row_offsets_concat: torch.Tensor, threads: int = 0, items_per_thread: int = 0,
+                 stream=None):
+        lib = ensure_loaded()
+        _need(row_offsets_concat, torch.int32, "row_offsets_concat")
+        self.ms = np.ascontiguousarray(ms, np.int32)
+        self.ns = np.ascontiguousarray(ns, np.int32)
+        self.nnzs = np.ascontiguousarray(nnzs, np.int32)
+        self.count = int(self.ms.shape[0])
+        self.total_rows = int(self.ms.astype(np.int64).sum())
+        self.total_cols = int(self.ns.astype(np.int64).sum())
+        self.total_nnz = int(self.nnzs.astype(np.int64).sum())
+        self._h = _P()
+        t = _tuning(threads, items_per_thread, 0)
+        _check(
+            lib.lb_batched_plan_create(self.count, self.ms.ctypes.data, self.ns.ctypes.data, self.nnzs.ctypes.data,
+                                       _ptr(row_offsets_concat), SCHEDULES["merge_path"], ctypes.byref(t), _stream(stream),
+                                       ctypes.byref(self._h)),
+            "lb_batched_plan_create",
+        )
+
+    def partition(self):
+        g = _I()
+        _check(_lib.lb_batched_plan_partition(self._h, None, None, ctypes.byref(g)), "lb_batched_plan_partition")
+        tr = np.empty(g.value + 1, np.int32)
+        tn = np.empty(g.value + 1, np.int32)
+        _check(_lib.lb_batched_plan_partition(self._h, tr.ctypes.data, tn.ctypes.data, ctypes.byref(g)), "lb_batched_plan_partition")
+        return tr, tn
+
+    def spmv(self, col_idx, values, x, out=None, stream=None) -> torch.Tensor:
+        _need(col_idx, torch.int32, "col_idx", self.total_nnz)
+        _need(values, None, "values", self.total_nnz)
+        _need(x, torch.float32, "x", self.total_cols)
+        y = torch.empty(self.total_rows, dtype=torch.float32, device=x.device) if out is None else out
+        _need(y, torch.float32, "y", self.total_rows)
+        _check(_lib.lb_spmv_batched(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y), _stream(stream)),
+               "lb_spmv_batched")
+        return y
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.lb_batched_plan_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SpMV(torch.autograd.Function):
+    """y = A x with gradients for the values and for x.
+
+    Backward: dx = A^T g by merge-path over the plan's CSC view (built on first use),
+    dvalues = g[row] * x[col] per nonzero over the forward partition.
+    """
+
+    @staticmethod
+    def forward(ctx, values, x, plan: Plan, col_idx):
+        ctx.plan = plan
+        ctx.save_for_backward(values, x, col_idx)
+        return plan.spmv(col_idx, values.detach(), x.detach())
+
+    @staticmethod
+    def backward(ctx, g):
+        values, x, col_idx = ctx.saved_tensors
+        plan = ctx.plan
+        g = g.contiguous().float()
+        dvals = dx = None
+        if ctx.needs_input_grad[0]:
+            dvals = plan.dvalues(col_idx, g, x.detach())
+            if values.dtype != torch.float32:
+                dvals = dvals.to(values.dtype)
+        if ctx.needs_input_grad[1]:
+            if not plan.has_transpose:
+                plan.build_transpose(col_idx)
+            dx = plan.spmv_t(values.detach(), g)
+        return dvals, dx, None, None
+
+
+def spmv_autograd(plan: Plan, col_idx, values, x):
+    """Differentiable y = A x (see ``SpMV``)."""
+    return SpMV.apply(values, x, plan, col_idx)
+
+
+def validate_csr(row_offsets, col_idx, n: int, check_sorted: bool = True, stream=None) -> int:
+    """Bit mask of problems found on the device (0 = valid); synchronizes to read it."""
+    lib = ensure_loaded()
+    m = row_offsets.numel() - 1
+    nnz = col_idx.numel()
+    status = torch.zeros(1, dtype=torch.int32, device=row_offsets.device)
+    _check(lib.lb_validate_csr(m, n, nnz, _ptr(row_offsets), _ptr(col_idx) if nnz else None, int(check_sorted), _ptr(status),
+                               _stream(stream)), "lb_validate_csr")
+    return int(status.item())
+
+
+def device_error(clear: bool = True) -> int:
+    """The device error word (0 or LB_ERR_TIMEOUT); synchronizes."""
+    lib = ensure_loaded()
+    s = _I()
+    _check(lib.lb_device_error(ctypes.byref(s), int(clear)), "lb_device_error")
+    return s.value
+
+
+def set_profile_events(before: torch.cuda.Event | None, after: torch.cuda.Event | None):
+    """Record `before`/`after` around every merge-path main kernel (None to stop)."""
+    lib = ensure_loaded()
+    b = before.cuda_event if before is not None else None
+    a = after.cuda_event if after is not None else None
+    _check(lib.lb_set_profile_events(b, a), "lb_set_profile_events")

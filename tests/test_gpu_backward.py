@@ -1,0 +1,145 @@
+"""Backward on the GPU vs the oracle: the CSC plan (stable transpose and its partition)
+bit-exact; dx = A^T g within 1e-5 * sum_i |a_ij||g_i| per column; dvalues = g[row] x[col]
+bit-exact (one rounding of an exact product); autograd end to end."""
+import numpy as np
+import pytest
+import torch
+
+from golden.fixtures import load
+from gpu_helpers import check_bound, dev, rounded, to_dev, vec, workload
+from paper_2212_08964_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def _plan_with_t(lb, a, schedule="merge_path", dtype=torch.float32, **tune):
+    ro, ci, v = to_dev(a, dtype)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule=schedule, **tune)
+    plan.build_transpose(ci)
+    return plan, ci, v
+
+
+def _cases():
+    f = load("worked_example_4x4.txt")
+    worked = synth.CSR(4, 4, f["row_offsets"].astype(np.int32), f["col_idx"].astype(np.int32), f["values"].astype(np.float32))
+    rng = np.random.default_rng(11)
+    # Columns concentrated in a few: long columns and many empty ones.
+    skew = synth.csr_from_row_lengths(rng, 300, rng.integers(0, 40, 5000))
+    wide = synth.csr_from_row_lengths(rng, 70_000, rng.integers(0, 9, 3000))  # n > 2^16: three radix passes
+    return {"worked": worked, "powerlaw_4k": workload("powerlaw_4k"), "skew": skew, "wide": wide,
+            "stencil_small": synth.stencil7_csr(12, seed=3)}
+
+
+@pytest.mark.parametrize("name", ["worked", "powerlaw_4k", "skew", "wide", "stencil_small"])
+def test_transpose_and_its_partition_bit_exact(lb, orc, name):
+    a = _cases()[name]
+    plan, _, _ = _plan_with_t(lb, a)
+    co, ri, perm = plan.transpose()
+    oco, ori, operm = orc.transpose(a.row_offsets, a.col_idx, a.n)
+    assert np.array_equal(co, oco) and np.array_equal(ri, ori) and np.array_equal(perm, operm)
+    tr, tn = plan.partition(transposed=True)
+    otr, otn = orc.partition(oco, plan.info()["tile_items"])
+    assert np.array_equal(tr, otr) and np.array_equal(tn, otn)
+
+
+@pytest.mark.parametrize("name", ["worked", "powerlaw_4k", "skew", "wide", "stencil_small"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_spmv_t_and_dvalues(lb, orc, name, dtype):
+    a = _cases()[name]
+    plan, ci, v = _plan_with_t(lb, a, dtype=dtype)
+    g = vec(a.m, 201)
+    x = vec(a.n, 202)
+    dx = plan.spmv_t(v, dev(g))
+    dv = plan.dvalues(ci, dev(g), dev(x))
+    torch.cuda.synchronize()
+    vals = a.values if dtype == torch.float32 else rounded(a.values, dtype)
+    ref = orc.spmv_t(a.row_offsets, a.col_idx, vals, g, a.n)
+    scale = orc.col_absdot(a.row_offsets, a.col_idx, vals, g, a.n)
+    check_bound(dx.cpu().numpy(), ref, scale, TOL32, "columns")
+    dv_ref = orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32)
+    assert np.array_equal(dv.cpu().numpy(), dv_ref)
+
+
+@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped"])
+def test_autograd_function(lb, orc, sched):
+    a = workload("powerlaw_4k")
+    ro, ci, v = to_dev(a)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule=sched)
+    x = vec(a.n, 203)
+    g = vec(a.m, 204)
+    vt = v.clone().requires_grad_(True)
+    xt = dev(x).requires_grad_(True)
+    y = lb.spmv_autograd(plan, ci, vt, xt)
+    y.backward(dev(g))
+    torch.cuda.synchronize()
+    ref_dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
+    scale = orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n)
+    check_bound(xt.grad.cpu().numpy(), ref_dx, scale, TOL32, "columns")
+    assert np.array_equal(vt.grad.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+
+
+def test_autograd_quadratic_loss_gradient(lb, orc):
+    """L = 1/2 ||A x - t||^2 on the finite-difference-sized log-normal matrix: GPU gradients
+    against the oracle's (which finite differences pin in the CPU tests)."""
+    a = synth.lognormal_csr(256, 256, 2.5, 1.2, seed=4, l_max=256)
+    rng = np.random.default_rng(12)
+    x = rng.uniform(-1, 1, a.n).astype(np.float32)
+    t = rng.uniform(-1, 1, a.m).astype(np.float32)
+    ro, ci, v = to_dev(a)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    vt = v.clone().requires_grad_(True)
+    xt = dev(x).requires_grad_(True)
+    y = lb.spmv_autograd(plan, ci, vt, xt)
+    loss = 0.5 * ((y - dev(t)) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    g = orc.spmv(a.row_offsets, a.col_idx, a.values, x) - t
+    dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
+    dv = orc.dvalues(a.row_offsets, a.col_idx, g, x)
+    # g on the GPU carries the forward's error (<= 1e-5 * sum|a||x| per row) into both
+    # gradients, so the bound scale is |g| + sum|a||x| per row.
+    ys = orc.row_absdot(a.row_offsets, a.col_idx, a.values, x)
+    gs = np.abs(g) + ys
+    sdx = orc.col_absdot(a.row_offsets, a.col_idx, a.values, gs, a.n)
+    check_bound(xt.grad.cpu().numpy(), dx, sdx, 2e-5, "columns")
+    rows = np.repeat(np.arange(a.m), a.row_lengths())
+    sdv = gs[rows] * np.abs(x[a.col_idx])
+    check_bound(vt.grad.cpu().numpy(), dv, sdv, 2e-5, "nonzeros")
+
+
+def test_full_size_lognormal_1m(lb, orc):
+    """The differentiable configuration at full size: forward, dx and dvalues."""
+    a = workload("lognormal_1m")
+    plan, ci, v = _plan_with_t(lb, a)
+    x = vec(a.n, 4)
+    g = vec(a.m, 5)
+    y = plan.spmv(ci, v, dev(x))
+    dx = plan.spmv_t(v, dev(g))
+    dv = plan.dvalues(ci, dev(g), dev(x))
+    torch.cuda.synchronize()
+    ref_y = orc.spmv(a.row_offsets, a.col_idx, a.values, x)
+    check_bound(y.cpu().numpy(), ref_y, orc.row_absdot(a.row_offsets, a.col_idx, a.values, x), TOL32)
+    ref_dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
+    mx, med = check_bound(dx.cpu().numpy(), ref_dx, orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n), TOL32, "columns")
+    print(f"lognormal_1m dx: max rel err {mx:.3e} median {med:.3e}")
+    assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+    co, ri, perm = plan.transpose()
+    oco, ori, operm = orc.transpose(a.row_offsets, a.col_idx, a.n)
+    assert np.array_equal(co, oco) and np.array_equal(ri, ori) and np.array_equal(perm, operm)
+
+
+def test_full_size_powerlaw_4m_backward(lb, orc):
+    """Backward on the large power-law matrix, as the benchmark's step runs it."""
+    a = workload("powerlaw_4m")
+    plan, ci, v = _plan_with_t(lb, a)
+    x = vec(a.n, 1)
+    g = vec(a.m, 3)
+    dx = plan.spmv_t(v, dev(g))
+    dv = plan.dvalues(ci, dev(g), dev(x))
+    torch.cuda.synchronize()
+    ref_dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
+    mx, med = check_bound(dx.cpu().numpy(), ref_dx, orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n), TOL32, "columns")
+    print(f"powerlaw_4m dx: max rel err {mx:.3e} median {med:.3e}")
+    assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
