@@ -62,9 +62,10 @@ typedef enum {
 typedef enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 } lb_dtype;
 
 /* Launch shape of a schedule; 0 selects the default.
- *   merge-path:   (threads, items_per_thread) in {(128, 8), (256, 4), (256, 8), (256, 12),
- *                 (256, 16), (512, 8)}, default (256, 8); one tile holds
- *                 threads * items_per_thread work items (rows + nonzeros);
+ *   merge-path:   (threads, items_per_thread) in {(128, 16), (256, 8), (256, 12), (256, 16),
+ *                 (384, 8), (512, 8)}, default (256, 8).  `threads` counts the gather threads
+ *                 of a CTA (scan and producer warps are added); one tile holds
+ *                 threads * items_per_thread - 8 work items (rows + nonzeros);
  *   block-mapped: threads in {128, 256} (the group is the block);
  *   group-mapped: group_size in {4, 8, 16, 32}. */
 typedef struct {
@@ -177,6 +178,10 @@ void lb_plan_destroy(lb_plan *p);
 lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, const int *h_nnz,
                                  const int *row_offsets_concat, lb_schedule s, const lb_tuning *t,
                                  cudaStream_t stream, lb_batched_plan **out);
+
+/* Launch shape, number of tiles and work items per tile of a batched plan (any output may
+ * be NULL). */
+lb_status lb_batched_plan_info(const lb_batched_plan *p, lb_tuning *t, int *num_tiles, int *tile_items);
 
 /* Copy the global partition to HOST arrays of num_tiles + 1 ints (synchronizes). */
 lb_status lb_batched_plan_partition(const lb_batched_plan *p, int *tile_row, int *tile_nz,

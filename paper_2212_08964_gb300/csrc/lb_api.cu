@@ -40,7 +40,7 @@ int *device_error_word() {
 }
 
 bool merge_shape_ok(int threads, int ipt) {
-    static const int shapes[][2] = {{128, 8}, {256, 4}, {256, 8}, {256, 12}, {256, 16}, {512, 8}};
+    static const int shapes[][2] = {{128, 16}, {256, 8}, {256, 12}, {256, 16}, {384, 8}, {512, 8}};
     for (const auto &s : shapes)
         if (s[0] == threads && s[1] == ipt) return true;
     return false;
@@ -113,6 +113,10 @@ bool sizes_ok(int m, int n, int nnz) {
     return true;
 }
 
+// Work items per merge-path tile: threads * items_per_thread slots, less 8 kept for the
+// lead of a tile's first nonzero past a 16-byte boundary.
+int merge_tile_items(int threads, int ipt) { return threads * ipt - 8; }
+
 int num_tiles_of(long long m, long long nnz, int tile_items) {
     const long long W = m + nnz;
     return static_cast<int>((W + tile_items - 1) / tile_items);
@@ -142,6 +146,9 @@ struct lb_plan {
     int *co = nullptr, *ri = nullptr, *perm = nullptr;
     int *t_tile_row = nullptr, *t_tile_nz = nullptr, *t_carry_row = nullptr;
     float *t_carry_val = nullptr;
+    int bucket_shift = 0;  // 0: values are gathered straight through perm (one L2-sized bucket)
+    int *bucket_pos = nullptr, *bucket_perm = nullptr;
+    void *bucket_vals = nullptr;  // per-call CSR values in bucket order (4 bytes per entry)
 };
 
 struct lb_batched_plan {
@@ -156,23 +163,26 @@ struct lb_batched_plan {
     float *carry_val = nullptr;
 };
 
-static void free_plan_arrays(lb_plan *p) {
-    int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row, p->co, p->ri, p->perm, p->t_tile_row,
-                   p->t_tile_nz, p->t_carry_row};
-    for (int *q : ints)
-        if (q) cudaFree(q);
-    if (p->carry_val) cudaFree(p->carry_val);
-    if (p->t_carry_val) cudaFree(p->t_carry_val);
-}
-
 static void release_transpose(lb_plan *p) {
-    int **ints[] = {&p->co, &p->ri, &p->perm, &p->t_tile_row, &p->t_tile_nz, &p->t_carry_row};
+    int **ints[] = {&p->co, &p->ri, &p->perm, &p->t_tile_row, &p->t_tile_nz, &p->t_carry_row, &p->bucket_pos,
+                    &p->bucket_perm};
     for (int **q : ints) {
         if (*q) cudaFree(*q);
         *q = nullptr;
     }
     if (p->t_carry_val) cudaFree(p->t_carry_val);
     p->t_carry_val = nullptr;
+    if (p->bucket_vals) cudaFree(p->bucket_vals);
+    p->bucket_vals = nullptr;
+    p->bucket_shift = 0;
+}
+
+static void free_plan_arrays(lb_plan *p) {
+    release_transpose(p);
+    int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row};
+    for (int *q : ints)
+        if (q) cudaFree(q);
+    if (p->carry_val) cudaFree(p->carry_val);
 }
 
 static bool on_device(int dev) {
@@ -235,7 +245,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
     if (s != LB_SCHED_MERGE_PATH) return from_cuda(launch_mapped(s, t, vdt, m, row_offsets, col_idx, values, x, y, stream));
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
-    const int T = t.threads * t.items_per_thread;
+    const int T = merge_tile_items(t.threads, t.items_per_thread);
     const int G = num_tiles_of(m, nnz, T);
     // Workspace: tile_row[G+1], tile_nz[G+1], carry_row[G], carry_val[G].
     const size_t bytes = (2 * (static_cast<size_t>(G) + 1) + static_cast<size_t>(G)) * sizeof(int) +
@@ -252,6 +262,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
         MergeArgs a{};
         a.num_tiles = G;
         a.num_rows = m;
+    a.num_atoms = nnz;
         a.tile_row = tile_row;
         a.tile_nz = tile_nz;
         a.row_end = row_offsets + 1;
@@ -287,7 +298,7 @@ lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_sched
     // The forward partition is built for every schedule (dvalues and the transpose use it).
     const int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
     const int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
-    p->tile_items = threads * ipt;
+    p->tile_items = merge_tile_items(threads, ipt);
     p->G = num_tiles_of(m, nnz, p->tile_items);
     cudaError_t e = cudaSuccess;
     if ((e = dmalloc(&p->ro, static_cast<size_t>(m) + 1)) != cudaSuccess ||
@@ -357,6 +368,7 @@ lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *valu
     MergeArgs a{};
     a.num_tiles = p->G;
     a.num_rows = p->m;
+    a.num_atoms = p->nnz;
     a.tile_row = p->tile_row;
     a.tile_nz = p->tile_nz;
     a.row_end = p->ro + 1;
@@ -405,6 +417,16 @@ lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t s
     }
     TransposeOut out{p->co, p->ri, p->perm};
     e = build_transpose(p->m, n, nnz, p->ro, col_idx, p->G, p->tile_items, p->tile_row, p->tile_nz, out, stream);
+    if (e == cudaSuccess && nnz > 0) {
+        const int shift = value_bucket_shift(nnz);
+        if (((static_cast<long long>(nnz) - 1) >> shift) > 0) {  // more than one bucket
+            p->bucket_shift = shift;
+            if ((e = dmalloc(&p->bucket_pos, static_cast<size_t>(nnz))) == cudaSuccess &&
+                (e = dmalloc(&p->bucket_perm, static_cast<size_t>(nnz))) == cudaSuccess &&
+                (e = cudaMalloc(&p->bucket_vals, static_cast<size_t>(nnz) * 4)) == cudaSuccess)
+                e = build_value_buckets(nnz, shift, p->perm, p->bucket_pos, p->bucket_perm, stream);
+        }
+    }
     if (e == cudaSuccess) {
         if (n > 0) {
             e = launch_partition(n, nnz, p->co, p->tile_items, p->t_tile_row, p->t_tile_nz, stream);
@@ -446,12 +468,21 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
     MergeArgs a{};
     a.num_tiles = p->Gt;
     a.num_rows = p->n;
+    a.num_atoms = p->nnz;
     a.tile_row = p->t_tile_row;
     a.tile_nz = p->t_tile_nz;
     a.row_end = p->co + 1;
     a.idx = p->ri;
     a.val = values;
     a.perm = p->perm;
+    if (p->bucket_shift > 0) {
+        // Values into bucket order first; the transposed kernel then gathers within L2.
+        const int eb = vdt == LB_F32 ? 4 : 2;
+        cudaError_t e = launch_bucket_values(p->nnz, eb, values, p->bucket_pos, p->bucket_vals, stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        a.val = p->bucket_vals;
+        a.perm = p->bucket_perm;
+    }
     a.x = g;
     a.y = dx;
     a.carry_row = p->t_carry_row;
@@ -517,7 +548,7 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     p->total_cols = cols;
     p->total_nnz = nnz;
     p->tune = r;
-    p->tile_items = r.threads * r.items_per_thread;
+    p->tile_items = merge_tile_items(r.threads, r.items_per_thread);
     p->G = num_tiles_of(rows, nnz, p->tile_items);
     const int kc = p->kc;
     int *d_ro_pos = nullptr, *d_row_base = nullptr;
@@ -571,6 +602,14 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     return LB_OK;
 }
 
+lb_status lb_batched_plan_info(const lb_batched_plan *p, lb_tuning *t, int *num_tiles, int *tile_items) {
+    if (!p) return LB_ERR_INVALID_ARG;
+    if (t) *t = p->tune;
+    if (num_tiles) *num_tiles = p->G;
+    if (tile_items) *tile_items = p->tile_items;
+    return LB_OK;
+}
+
 lb_status lb_batched_plan_partition(const lb_batched_plan *p, int *tile_row, int *tile_nz, int *num_tiles) {
     if (!p || !num_tiles) return LB_ERR_INVALID_ARG;
     *num_tiles = p->G;
@@ -597,6 +636,7 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, c
     MergeArgs a{};
     a.num_tiles = p->G;
     a.num_rows = static_cast<int>(p->total_rows);
+    a.num_atoms = static_cast<int>(p->total_nnz);
     a.tile_row = p->tile_row;
     a.tile_nz = p->tile_nz;
     a.row_end = p->ro_g + 1;

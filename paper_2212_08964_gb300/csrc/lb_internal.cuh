@@ -52,6 +52,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -128,6 +132,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 struct MergeArgs {
     int num_tiles;        // G
     int num_rows;         // rows of the set (y has this many entries)
+    int num_atoms;        // atoms of the set (entries of idx, and of val or perm)
     const int *tile_row;  // [G+1] row ends consumed before each tile boundary
     const int *tile_nz;   // [G+1] atoms consumed before each tile boundary
     const int *row_end;   // row_end[r] = offset one past the last atom of row r (offsets + 1)
@@ -184,6 +189,17 @@ struct TransposeOut {
 cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci, int num_tiles,
                             int tile_items, const int *tile_row, const int *tile_nz, TransposeOut out,
                             cudaStream_t stream);
+
+// L2-sized buckets for bringing CSR-ordered values into CSC order (see lb_transpose.cu).
+// log2 of the bucket size in CSC entries; one bucket means no bucketing is needed.
+int value_bucket_shift(long long nnz);
+// bucket_pos[k] (position of CSR entry k in bucket order) and bucket_perm[p] (position in
+// bucket order of the value CSC entry p needs), from perm.
+cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket_pos, int *bucket_perm,
+                                cudaStream_t stream);
+// tmp[bucket_pos[k]] = values[k] for every k (element size 2 or 4 bytes).
+cudaError_t launch_bucket_values(int nnz, int elem_bytes, const void *values, const int *bucket_pos, void *tmp,
+                                 cudaStream_t stream);
 
 // Batched-plan helpers.
 cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *row_base, const int *nz_base,

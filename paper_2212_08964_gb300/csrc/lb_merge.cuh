@@ -1,4 +1,4 @@
-// lb_merge.cuh -- persistent merge-path SpMV (work-oriented schedule) for sm_103a.
+// lb_merge.cuh -- persistent, warp-specialized merge-path SpMV (work-oriented schedule) for sm_103a.
 //
 // The schedule is the dissertation's work-oriented merge path (Ch.3 Sec. "Work-Oriented",
 // Alg. alg:work-oriented; Ch.4 Sec. "Merge-path load balancing"): rows and nonzeros count
@@ -6,69 +6,141 @@
 // split of the merge of row ends with nonzero indices gives every tile its starting row and
 // nonzero.  Rows completed inside a tile are written directly; the row left open at the end
 // of a tile goes out as a carry and is added by the fixup pass ("Fix-up" procedure of the
-// same algorithm).  The split is hierarchical as the paper describes: tiles over the whole
-// matrix (computed once by the partition kernel), then threads inside a tile by a second
-// merge-path search over shared memory.
+// same algorithm).  The tile-level split is computed once by the partition kernel.
 //
-// GB300 realisation (not in the paper, which targets V100):
-//   * persistent CTAs (one wave of resident CTAs) stride over fixed-size tiles, so the
-//     partition and the summation order do not depend on the SM count;
-//   * each tile's row ends, column indices and values are staged in shared memory by 1-D
-//     bulk TMA copies (cp.async.bulk + mbarrier), double-buffered so the next tile streams in
-//     while the current one computes; the ragged (< 16 B) ends of each array slice are
-//     fetched with plain loads, so any pointer alignment works;
-//   * the streamed arrays carry an L2 evict-first hint, leaving L2 to the gathered x;
-//   * products are formed with all of a thread's gathers in flight, then the per-thread
-//     carries are combined by a block-wide segmented scan (warp shuffles + one shared-memory
-//     step) instead of atomics, so results are deterministic;
-//   * completed rows are staged in shared memory and written to y with coalesced stores.
+// Inside a tile the paper splits the work again, by a second merge-path search per thread,
+// and walks row ends and nonzeros one by one.  This kernel keeps the tile split and computes
+// the same row sums with a segmented scan over the tile's nonzeros: products, one bit per
+// position where a row starts, a scan that restarts at those bits, and each row's sum read at
+// its last nonzero.  No atomics touch y and the summation order is fixed, so results are
+// deterministic.
+//
+// GB300 realisation.  Random 4-byte gathers of x are the limiting resource (the L1 handles
+// one scattered sector per cycle), so the kernel is organised to keep them issuing without
+// pause, with three warp roles per CTA connected by shared-memory mbarriers:
+//   * a producer warp moves each tile's row ends, indices and values into a shared-memory
+//     stage with 1-D bulk TMA copies (three stages in flight);
+//   * gather warps (GW) read their IPT consecutive slots of a staged tile with vector loads,
+//     gather x, and store the products into one of two product buffers;
+//   * scan warps (SW) mark row starts, scan the products in blocked order (IPT_S slots per
+//     thread, warp shuffles, one shared-memory step), write the finished rows to y with
+//     coalesced stores and the open row's partial sum as the tile's carry.
+// Stages and product buffers are recycled through "done" barriers, so no role waits for
+// another except when a buffer is genuinely empty or full.  Every wait is bounded: a kernel
+// that gives up records LB_ERR_TIMEOUT and returns.
+//
+// Persistent CTAs (one wave) take tiles blockIdx.x + i * gridDim.x, so the partition and the
+// summation order do not depend on the SM count.  Shared memory mirrors global addresses
+// modulo 16: a slice whose 16-byte aligned superset lies inside its array moves with one bulk
+// copy; slices touching an array's first or last 8 elements also move their ragged ends with
+// plain loads.  The streamed arrays carry an L2 evict-first hint, leaving L2 to x.
 #pragma once
 
 #include <mutex>
+#include <type_traits>
 
 #include "lb_internal.cuh"
 
 namespace lb {
 
-template <int THREADS, int IPT, int SV>
+// Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.
+template <int GW, int IPT, int SV>
 struct MergeShape {
-    static constexpr int T = THREADS * IPT;  // work items per tile
-    static constexpr int WARPS = THREADS / 32;
-    // One stage: row ends (4 B per row), indices (4 B per atom), values or perm (SV B per
-    // atom), each padded to 16 B at both ends.  rows + atoms <= T.
+    static_assert(IPT % 4 == 0, "items per thread must be a multiple of 4 (128-bit shared loads)");
+    static constexpr int GT = GW * 32;   // gather threads
+    static constexpr int T = GT * IPT;   // slots per tile
+    // Work items per tile: a tile's first nonzero sits up to 7 slots past a 16-byte boundary,
+    // so 8 slots are kept free for that lead.
+    static constexpr int TILE_ITEMS = T - 8;
+    static constexpr int SIPT = 16;      // scan slots per scan thread
+    static_assert(T % (SIPT * 32) == 0, "tile must split into whole scan warps");
+    static constexpr int SW = T / (SIPT * 32);  // scan warps
+    static constexpr int ST = SW * 32;          // scan threads
+    static constexpr int THREADS = GT + ST + 32;  // + one producer warp
+    static constexpr int NSTAGE = 3;
+    // One stage: row ends (4 B per row), indices (4 B per atom), values or CSR positions
+    // (SV B per atom), each padded to 16 B at both ends.  rows + atoms <= T.
     static constexpr int STAGE = ((4 + SV) * T + 128 + 127) / 128 * 128;
-    static constexpr size_t SMEM = 128 + 2 * (size_t)STAGE + (size_t)T * 4 + 2 * 32 * 4;
+    static constexpr int BITS_WORDS = T / 32 + 2;
+    static constexpr int P_FLOATS = T + (T / 32) * 4;  // products with 4 floats of padding per 32
+    static constexpr int HDR = 512;                    // mbarriers + stage headers
+    static constexpr size_t SMEM = HDR + NSTAGE * static_cast<size_t>(STAGE) + 2 * static_cast<size_t>(P_FLOATS) * 4 +
+                                   BITS_WORDS * 4 + 2 * 32 * 4;
+    // Resident CTAs per SM from shared memory (228 KB per SM, 1 KB reserved per CTA), capped
+    // by a register budget of 56 per thread.
+    static constexpr int BY_SMEM = static_cast<int>((228 * 1024) / (SMEM + 1024));
+    static constexpr int BY_REGS = 65536 / (THREADS * 56);
+    static constexpr int MIN_BLOCKS_RAW = BY_SMEM < BY_REGS ? BY_SMEM : BY_REGS;
+    static constexpr int MIN_BLOCKS = MIN_BLOCKS_RAW < 1 ? 1 : MIN_BLOCKS_RAW;
 };
 
-// Where one array slice [e_lo, e_hi) lands in a stage.  Shared memory mirrors the global
-// byte address modulo 16, so the 16-byte-aligned middle of the slice moves with one bulk copy
-// and at most 15 bytes at each end move with plain loads.
+// Index of slot j in a padded product buffer: 4 floats of padding after every 32 keep the
+// blocked 128-bit accesses free of bank conflicts.
+__device__ __forceinline__ int ppad(int j) { return j + ((j >> 5) << 2); }
+
+// Per-stage header written by the producer before it arms the stage's mbarrier.
+struct StageHdr {
+    int r0, r1, k0, k1, m0, m1;
+    uint32_t re_first, idx_first, val_first;
+    int ok;
+};
+
+// Shared-memory mbarriers of one CTA.
+struct Bars {
+    uint64_t full[3];    // stage s holds tile data (producer arm + TMA bytes)
+    uint64_t gdone[3];   // gather warps finished reading stage s (one arrival per gather warp)
+    uint64_t sdone[3];   // scan warps finished with stage s (one arrival)
+    uint64_t pready[2];  // product buffer b filled (one arrival per gather warp)
+    uint64_t pfree[2];   // product buffer b consumed (one arrival)
+};
+
+// Where one array slice [e_lo, e_hi) of an array holding n_elems elements lands in a stage.
 struct Seg {
     uint32_t first;       // stage offset of element e_lo
     uint32_t next;        // 16-byte-aligned stage offset after this slice
-    uint32_t head;        // elements before the bulk part
-    uint32_t tail;        // first element after the bulk part
+    uint32_t bulk_off;    // stage offset of the bulk copy
+    uint32_t bulk_bytes;  // bytes moved by TMA (multiple of 16, may be 0)
+    uint32_t head;        // elements [0, head) of the slice move by plain loads
+    uint32_t tail;        // elements [tail, count) of the slice move by plain loads
     uint32_t count;       // elements in the slice
-    uint32_t bulk_bytes;  // bytes in the bulk part (multiple of 16, may be 0)
-    uintptr_t bulk_src;   // global address of the bulk part
+    uintptr_t bulk_src;   // global address of the bulk copy
 };
 
-__device__ __forceinline__ Seg make_seg(const void *base, long long e_lo, long long e_hi, uint32_t sz, uint32_t off) {
-    const uintptr_t lo = reinterpret_cast<uintptr_t>(base) + static_cast<uintptr_t>(e_lo) * sz;
-    const uintptr_t hi = reinterpret_cast<uintptr_t>(base) + static_cast<uintptr_t>(e_hi) * sz;
+__device__ __forceinline__ Seg make_seg(const void *base, long long e_lo, long long e_hi, long long n_elems,
+                                        uint32_t sz, uint32_t off) {
+    const uintptr_t b = reinterpret_cast<uintptr_t>(base);
+    const uintptr_t lo = b + static_cast<uintptr_t>(e_lo) * sz;
+    const uintptr_t hi = b + static_cast<uintptr_t>(e_hi) * sz;
     const uintptr_t a0 = lo & ~static_cast<uintptr_t>(15);
-    uintptr_t A = (lo + 15) & ~static_cast<uintptr_t>(15);
-    if (A > hi) A = hi;
-    uintptr_t B = hi & ~static_cast<uintptr_t>(15);
-    if (B < A) B = A;
+    const uintptr_t a1 = (hi + 15) & ~static_cast<uintptr_t>(15);
     Seg s;
     s.first = off + static_cast<uint32_t>(lo - a0);
-    s.next = off + static_cast<uint32_t>(((hi + 15) & ~static_cast<uintptr_t>(15)) - a0);
-    s.head = static_cast<uint32_t>((A - lo) / sz);
-    s.tail = static_cast<uint32_t>((B - lo) / sz);
+    s.next = off + static_cast<uint32_t>(a1 - a0);
     s.count = static_cast<uint32_t>(e_hi - e_lo);
-    s.bulk_bytes = static_cast<uint32_t>(B - A);
-    s.bulk_src = A;
+    if (e_hi <= e_lo) {
+        s.bulk_off = off;
+        s.bulk_bytes = 0;
+        s.head = 0;
+        s.tail = 0;
+        s.bulk_src = a0;
+    } else if (a0 >= b && a1 <= b + static_cast<uintptr_t>(n_elems) * sz) {
+        // The aligned superset stays inside the array: one bulk copy, no plain loads.
+        s.bulk_off = off;
+        s.bulk_bytes = static_cast<uint32_t>(a1 - a0);
+        s.head = 0;
+        s.tail = s.count;
+        s.bulk_src = a0;
+    } else {
+        uintptr_t A = (lo + 15) & ~static_cast<uintptr_t>(15);
+        if (A > hi) A = hi;
+        uintptr_t B = hi & ~static_cast<uintptr_t>(15);
+        if (B < A) B = A;
+        s.head = static_cast<uint32_t>((A - lo) / sz);
+        s.tail = static_cast<uint32_t>((B - lo) / sz);
+        s.bulk_bytes = static_cast<uint32_t>(B - A);
+        s.bulk_off = s.first + s.head * sz;
+        s.bulk_src = A;
+    }
     return s;
 }
 
@@ -80,78 +152,19 @@ struct MergeTraits {
     }
 };
 
-struct TileSegs {
-    Seg re, idx, val;
-};
-
-template <typename V, int MODE>
-__device__ __forceinline__ TileSegs tile_segs(const MergeArgs &a, int r0, int r1, int k0, int k1) {
-    TileSegs t;
-    t.re = make_seg(a.row_end, r0, r1, 4, 0);
-    t.idx = make_seg(a.idx, k0, k1, 4, t.re.next);
-    t.val = make_seg(MergeTraits<V, MODE>::third(a), k0, k1, MergeTraits<V, MODE>::SV, t.idx.next);
-    return t;
-}
-
-__device__ __forceinline__ void copy_ragged(unsigned char *stage, uint32_t first, const void *gfirst, uint32_t sz,
-                                            uint32_t rel) {
-    const char *src = static_cast<const char *>(gfirst) + static_cast<size_t>(rel) * sz;
-    unsigned char *dst = stage + first + rel * sz;
-    if (sz == 4)
-        *reinterpret_cast<int *>(dst) = __ldg(reinterpret_cast<const int *>(src));
-    else
-        *reinterpret_cast<unsigned short *>(dst) = __ldg(reinterpret_cast<const unsigned short *>(src));
-}
-
-// A tile from a valid partition has rows + atoms <= T; anything else means the offsets were
-// not a valid CSR prefix sum, and the tile is skipped rather than overflow shared memory.
+// A tile from a valid partition has rows + atoms <= TILE_ITEMS; anything else means the
+// offsets were not a valid CSR prefix sum, and the tile is skipped rather than overflow
+// shared memory.
 template <int T_ITEMS>
 __device__ __forceinline__ bool tile_ok(int r0, int r1, int k0, int k1) {
     const int nr = r1 - r0, nk = k1 - k0;
     return nr >= 0 && nk >= 0 && nr + nk <= T_ITEMS;
 }
 
-// Start moving tile [r0, r1) x [k0, k1) into `stage`: thread 0 issues the bulk copies, threads
-// 0..47 copy the ragged ends (at most 7 elements per end and array).
-template <typename V, int MODE, int T_ITEMS>
-__device__ __forceinline__ void stage_tile(const MergeArgs &a, unsigned char *stage, uint64_t *bar, int r0, int r1,
-                                           int k0, int k1, uint64_t pol) {
-    const int tid = threadIdx.x;
-    if (!tile_ok<T_ITEMS>(r0, r1, k0, k1)) {  // malformed offsets: stage nothing
-        if (tid == 0) mbar_arrive_expect_tx(bar, 0);
-        return;
-    }
-    const TileSegs t = tile_segs<V, MODE>(a, r0, r1, k0, k1);
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, t.re.bulk_bytes + t.idx.bulk_bytes + t.val.bulk_bytes);
-        if (t.re.bulk_bytes)
-            bulk_g2s(stage + t.re.first + t.re.head * 4u, reinterpret_cast<const void *>(t.re.bulk_src),
-                     t.re.bulk_bytes, bar, pol);
-        if (t.idx.bulk_bytes)
-            bulk_g2s(stage + t.idx.first + t.idx.head * 4u, reinterpret_cast<const void *>(t.idx.bulk_src),
-                     t.idx.bulk_bytes, bar, pol);
-        if (t.val.bulk_bytes)
-            bulk_g2s(stage + t.val.first + t.val.head * MergeTraits<V, MODE>::SV,
-                     reinterpret_cast<const void *>(t.val.bulk_src), t.val.bulk_bytes, bar, pol);
-    }
-    if (tid < 48) {
-        const int which = tid >> 4;
-        const bool tail = ((tid >> 3) & 1) != 0;
-        const uint32_t e = tid & 7;
-        const uint32_t first = which == 0 ? t.re.first : (which == 1 ? t.idx.first : t.val.first);
-        const uint32_t head = which == 0 ? t.re.head : (which == 1 ? t.idx.head : t.val.head);
-        const uint32_t tl = which == 0 ? t.re.tail : (which == 1 ? t.idx.tail : t.val.tail);
-        const uint32_t count = which == 0 ? t.re.count : (which == 1 ? t.idx.count : t.val.count);
-        const uint32_t sz = which == 2 ? MergeTraits<V, MODE>::SV : 4u;
-        const void *gfirst =
-            which == 0 ? static_cast<const void *>(a.row_end + r0)
-                       : (which == 1 ? static_cast<const void *>(a.idx + k0)
-                                     : static_cast<const void *>(static_cast<const char *>(MergeTraits<V, MODE>::third(a)) +
-                                                                 static_cast<size_t>(k0) * sz));
-        const uint32_t rel = tail ? tl + e : e;
-        const bool ok = tail ? (rel < count) : (e < head);
-        if (ok) copy_ragged(stage, first, gfirst, sz, rel);
-    }
+// A slice whose aligned superset stays inside its array moves entirely by TMA; only tiles
+// touching the first or last 8 elements of an array can need plain loads.
+__device__ __forceinline__ bool edge_tile(const MergeArgs &a, int r0, int r1, int k0, int k1) {
+    return r0 < 8 || r1 > a.num_rows - 8 || k0 < 8 || k1 > a.num_atoms - 8;
 }
 
 struct TileBounds {
@@ -174,6 +187,117 @@ __device__ __forceinline__ TileBounds load_bounds(const MergeArgs &a, int tile) 
     return b;
 }
 
+// Producer: move tile b into `stage` and arm its mbarrier (all 32 lanes of the producer warp
+// call this; lane 0 writes the header and arms the barrier).
+template <typename V, int MODE, int T_ITEMS>
+__device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, StageHdr *hdr, unsigned char *stage,
+                                             const TileBounds &b, uint64_t pol) {
+    const int lane = threadIdx.x & 31;
+    // Earlier plain writes into this stage must be ordered before the new bulk writes.
+    fence_proxy_async_smem();
+    if (!tile_ok<T_ITEMS>(b.r0, b.r1, b.k0, b.k1)) {  // malformed offsets: stage nothing
+        if (lane == 0) {
+            hdr->r0 = b.r0;
+            hdr->r1 = b.r1;
+            hdr->k0 = b.k0;
+            hdr->k1 = b.k1;
+            hdr->ok = 0;
+            mbar_arrive_expect_tx(bar, 0);
+        }
+        return;
+    }
+    constexpr uint32_t SV = MergeTraits<V, MODE>::SV;
+    if (!edge_tile(a, b.r0, b.r1, b.k0, b.k1)) {
+        // Interior tile: every slice's aligned superset lies inside its array.  Lanes 0, 1, 2
+        // each place one slice (row ends, indices, values).
+        if (lane < 3) {
+            const uintptr_t base = lane == 0 ? reinterpret_cast<uintptr_t>(a.row_end)
+                                             : (lane == 1 ? reinterpret_cast<uintptr_t>(a.idx)
+                                                          : reinterpret_cast<uintptr_t>(MergeTraits<V, MODE>::third(a)));
+            const uint32_t sz = lane == 2 ? SV : 4u;
+            const uint32_t e_lo = static_cast<uint32_t>(lane == 0 ? b.r0 : b.k0);
+            const uint32_t e_hi = static_cast<uint32_t>(lane == 0 ? b.r1 : b.k1);
+            const uintptr_t lo = base + static_cast<uintptr_t>(e_lo) * sz;
+            const uintptr_t hi = base + static_cast<uintptr_t>(e_hi) * sz;
+            const uintptr_t a0 = lo & ~static_cast<uintptr_t>(15);
+            const uint32_t bytes = static_cast<uint32_t>(((hi + 15) & ~static_cast<uintptr_t>(15)) - a0);
+            const uint32_t b1 = __shfl_up_sync(0x7u, bytes, 1);
+            const uint32_t b2 = __shfl_up_sync(0x7u, bytes, 2);
+            const uint32_t off = (lane >= 1 ? b1 : 0u) + (lane >= 2 ? b2 : 0u);
+            const uint32_t first = off + static_cast<uint32_t>(lo & 15);
+            const uint32_t total = __shfl_sync(0x7u, off + bytes, 2);
+            const uint32_t f1 = __shfl_sync(0x7u, first, 1);
+            const uint32_t f2 = __shfl_sync(0x7u, first, 2);
+            if (lane == 0) {
+                hdr->r0 = b.r0;
+                hdr->r1 = b.r1;
+                hdr->k0 = b.k0;
+                hdr->k1 = b.k1;
+                hdr->m0 = b.m0;
+                hdr->m1 = b.m1;
+                hdr->re_first = first;
+                hdr->idx_first = f1;
+                hdr->val_first = f2;
+                hdr->ok = 1;
+                mbar_arrive_expect_tx(bar, total);
+            }
+            __syncwarp(0x7u);  // the transaction count is armed before any copy lands
+            if (bytes) bulk_g2s(stage + off, reinterpret_cast<const void *>(a0), bytes, bar, pol);
+        }
+        return;
+    }
+    // Edge tile: general placement; the ragged ends (at most 7 elements per end and slice)
+    // move with plain loads by the producer lanes before the barrier is armed.
+    Seg t[3];
+    t[0] = make_seg(a.row_end, b.r0, b.r1, a.num_rows, 4, 0);
+    t[1] = make_seg(a.idx, b.k0, b.k1, a.num_atoms, 4, t[0].next);
+    t[2] = make_seg(MergeTraits<V, MODE>::third(a), b.k0, b.k1, a.num_atoms, SV, t[1].next);
+    for (int q = lane; q < 48; q += 32) {
+        const int which = q >> 4;
+        const bool tail = ((q >> 3) & 1) != 0;
+        const uint32_t e = q & 7;
+        // Fields picked by value (a dynamic index into t[] would put it in local memory).
+        const uint32_t g_first = which == 0 ? t[0].first : (which == 1 ? t[1].first : t[2].first);
+        const uint32_t g_head = which == 0 ? t[0].head : (which == 1 ? t[1].head : t[2].head);
+        const uint32_t g_tail = which == 0 ? t[0].tail : (which == 1 ? t[1].tail : t[2].tail);
+        const uint32_t g_count = which == 0 ? t[0].count : (which == 1 ? t[1].count : t[2].count);
+        const uint32_t sz = which == 2 ? SV : 4u;
+        const uint32_t rel = tail ? g_tail + e : e;
+        const bool ok = tail ? (rel < g_count) : (e < g_head);
+        if (!ok) continue;
+        const char *src = which == 0 ? reinterpret_cast<const char *>(a.row_end + b.r0)
+                                     : (which == 1 ? reinterpret_cast<const char *>(a.idx + b.k0)
+                                                   : static_cast<const char *>(MergeTraits<V, MODE>::third(a)) +
+                                                         static_cast<size_t>(b.k0) * sz);
+        src += static_cast<size_t>(rel) * sz;
+        unsigned char *dst = stage + g_first + rel * sz;
+        if (sz == 4)
+            *reinterpret_cast<int *>(dst) = __ldg(reinterpret_cast<const int *>(src));
+        else
+            *reinterpret_cast<unsigned short *>(dst) = __ldg(reinterpret_cast<const unsigned short *>(src));
+    }
+    __syncwarp();
+    if (lane == 0) {
+        hdr->r0 = b.r0;
+        hdr->r1 = b.r1;
+        hdr->k0 = b.k0;
+        hdr->k1 = b.k1;
+        hdr->m0 = b.m0;
+        hdr->m1 = b.m1;
+        hdr->re_first = t[0].first;
+        hdr->idx_first = t[1].first;
+        hdr->val_first = t[2].first;
+        hdr->ok = 1;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, t[0].bulk_bytes + t[1].bulk_bytes + t[2].bulk_bytes);
+#pragma unroll
+        for (int w = 0; w < 3; ++w)
+            if (t[w].bulk_bytes)
+                bulk_g2s(stage + t[w].bulk_off, reinterpret_cast<const void *>(t[w].bulk_src), t[w].bulk_bytes, bar,
+                         pol);
+    }
+}
+
 // Column base of nonzero k inside a tile whose nonzeros lie in matrices [m0, m1].
 __device__ __forceinline__ int batched_col_base(const MergeArgs &a, int m0, int m1, int k) {
     int lo = m0, hi = m1;
@@ -187,200 +311,360 @@ __device__ __forceinline__ int batched_col_base(const MergeArgs &a, int m0, int 
     return __ldg(a.mat_col_base + lo);
 }
 
-template <typename V, int THREADS, int IPT, int MODE>
-__global__ void __launch_bounds__(THREADS) merge_spmv_kernel(const MergeArgs a) {
-    using Sh = MergeShape<THREADS, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
-    constexpr int T = Sh::T;
+// A 16-bit value's bits widened to FP32 (BF16: shift into the high half; FP16: convert).
+template <typename V>
+__device__ __forceinline__ float half_bits_to_f32(unsigned short bits) {
+    if constexpr (std::is_same<V, __nv_bfloat16>::value)
+        return __uint_as_float(static_cast<uint32_t>(bits) << 16);
+    else
+        return __half2float(__ushort_as_half(bits));
+}
+
+// Blocked tile layout.  Slot s of a tile is element (16-byte-aligned start) + s of its index
+// slice in shared memory; the tile's first nonzero sits at slot `lead` (0..7).  Gather thread
+// g owns slots [g*IPT, (g+1)*IPT).  Slots outside [lead, lead + nk) are padding with product 0.
+__device__ __forceinline__ int tile_lead(const StageHdr &h) { return static_cast<int>(h.idx_first & 15u) >> 2; }
+
+// Products of gather thread g's slots of one tile (indices and values by vector shared loads,
+// all gathers in flight before the first use).
+template <typename V, int IPT, int MODE>
+__device__ __forceinline__ void gather_products(const MergeArgs &a, const unsigned char *stage, const StageHdr &h, int g,
+                                                float (&prod)[IPT]) {
+    const int nk = h.k1 - h.k0;
+    const int lead = tile_lead(h);
+    const int slot0 = g * IPT;
+    const int item0 = slot0 - lead;  // tile item of this thread's first slot
+    float vv[IPT], xv[IPT];
+    int col[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        col[q] = 0;
+        vv[q] = 0.f;
+        xv[q] = 0.f;
+        prod[q] = 0.f;
+    }
+    if (item0 + IPT <= 0 || item0 >= nk) return;  // nothing of the tile in this thread's slots
+    const unsigned char *idx0 = stage + h.idx_first - lead * 4;  // slot 0, 16-byte aligned
+#pragma unroll
+    for (int q = 0; q < IPT; q += 4) {
+        const int4 c = *reinterpret_cast<const int4 *>(idx0 + (slot0 + q) * 4);
+        col[q] = c.x;
+        col[q + 1] = c.y;
+        col[q + 2] = c.z;
+        col[q + 3] = c.w;
+    }
+    constexpr uint32_t SV = MergeTraits<V, MODE>::SV;
+    const unsigned char *val_item0 = stage + h.val_first;  // tile item 0
+    const uintptr_t vslot0 = reinterpret_cast<uintptr_t>(val_item0) - static_cast<uintptr_t>(lead) * SV;
+    if (SV == 4) {
+        int raw[IPT];
+        if ((vslot0 & 15u) == 0) {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4) {
+                const int4 t = *reinterpret_cast<const int4 *>(vslot0 + static_cast<uintptr_t>(slot0 + q) * 4);
+                raw[q] = t.x;
+                raw[q + 1] = t.y;
+                raw[q + 2] = t.z;
+                raw[q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int it = item0 + q;
+                raw[q] = (it >= 0 && it < nk) ? reinterpret_cast<const int *>(val_item0)[it] : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const int it = item0 + q;
+            if (it >= 0 && it < nk) {
+                if (MODE == kTransposed)
+                    vv[q] = to_f32(__ldg(static_cast<const V *>(a.val) + raw[q]));
+                else
+                    vv[q] = __int_as_float(raw[q]);
+            }
+        }
+    } else {
+        unsigned short raw[IPT];
+        if ((vslot0 & 15u) == 0 && IPT % 8 == 0) {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 8) {
+                const uint4 t = *reinterpret_cast<const uint4 *>(vslot0 + static_cast<uintptr_t>(slot0 + q) * 2);
+                const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    raw[q + 2 * e] = static_cast<unsigned short>(w[e] & 0xffffu);
+                    raw[q + 2 * e + 1] = static_cast<unsigned short>(w[e] >> 16);
+                }
+            }
+        } else if ((vslot0 & 7u) == 0) {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4) {
+                const uint2 t = *reinterpret_cast<const uint2 *>(vslot0 + static_cast<uintptr_t>(slot0 + q) * 2);
+                raw[q] = static_cast<unsigned short>(t.x & 0xffffu);
+                raw[q + 1] = static_cast<unsigned short>(t.x >> 16);
+                raw[q + 2] = static_cast<unsigned short>(t.y & 0xffffu);
+                raw[q + 3] = static_cast<unsigned short>(t.y >> 16);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int it = item0 + q;
+                raw[q] = (it >= 0 && it < nk) ? reinterpret_cast<const unsigned short *>(val_item0)[it] : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const int it = item0 + q;
+            if (it >= 0 && it < nk) vv[q] = half_bits_to_f32<V>(raw[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int it = item0 + q;
+        if (it >= 0 && it < nk) {
+            int c = col[q];
+            if (MODE == kBatched) c += batched_col_base(a, h.m0, h.m1, h.k0 + it);
+            xv[q] = __ldg(a.x + c);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) prod[q] = vv[q] * xv[q];
+}
+
+// Named barrier over the scan warps only (id 1).
+template <int NTHREADS>
+__device__ __forceinline__ void scan_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
+}
+
+// The same barrier with an OR vote, so the scan warps take the same branch.
+template <int NTHREADS>
+__device__ __forceinline__ bool scan_bar_any(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(pred)), "n"(NTHREADS)
+        : "memory");
+    return r != 0;
+}
+
+template <typename V, int GW, int IPT, int MODE>
+__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>::THREADS,
+                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>::MIN_BLOCKS)
+    merge_spmv_kernel(const MergeArgs a) {
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
+    constexpr int NS = Sh::NSTAGE;
+    constexpr int SIPT = Sh::SIPT;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    unsigned char *stages = smem + 128;
-    float *s_out = reinterpret_cast<float *>(smem + 128 + 2 * Sh::STAGE);
-    int *s_wf = reinterpret_cast<int *>(s_out + T);
+    Bars *bars = reinterpret_cast<Bars *>(smem);
+    StageHdr *hdrs = reinterpret_cast<StageHdr *>(smem + 256);
+    unsigned char *stages = smem + Sh::HDR;
+    float *s_p0 = reinterpret_cast<float *>(stages + NS * Sh::STAGE);  // product buffers (x2)
+    uint32_t *s_bits = reinterpret_cast<uint32_t *>(s_p0 + 2 * Sh::P_FLOATS);  // segment starts by slot
+    int *s_wf = reinterpret_cast<int *>(s_bits + Sh::BITS_WORDS);
     float *s_wv = reinterpret_cast<float *>(s_wf + 32);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int G = a.num_tiles;
-    int tile = blockIdx.x;
-    if (tile >= G) return;
+    if (static_cast<int>(blockIdx.x) >= G) return;
+    const int n_my = (G - static_cast<int>(blockIdx.x) + static_cast<int>(gridDim.x) - 1) / static_cast<int>(gridDim.x);
+    auto tile_of = [&](int i) { return static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x); };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int q = 0; q < 3; ++q) {
+            mbar_init(&bars->full[q], 1);
+            mbar_init(&bars->gdone[q], GW);
+            mbar_init(&bars->sdone[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&bars->pready[q], GW);
+            mbar_init(&bars->pfree[q], 1);
+        }
         mbar_fence_init();
     }
+    for (int w = tid; w < Sh::BITS_WORDS; w += Sh::THREADS) s_bits[w] = 0u;
     __syncthreads();
-    const uint64_t pol = policy_evict_first();
 
-    TileBounds cur = load_bounds<MODE>(a, tile);
-    stage_tile<V, MODE, T>(a, stages, &bar[0], cur.r0, cur.r1, cur.k0, cur.k1, pol);
-    int next_tile = tile + gridDim.x;
-    TileBounds nxt = {0, 0, 0, 0, 0, 0};
-    if (next_tile < G) nxt = load_bounds<MODE>(a, next_tile);
-    uint32_t phases = 0;
-
-    for (int it = 0; tile < G; ++it) {
-        const int s = it & 1;
-        unsigned char *stage = stages + s * Sh::STAGE;
-
-        // Stream the next tile into the other stage; fetch the bounds of the one after.
-        const int after_tile = next_tile + gridDim.x;
-        TileBounds aft = {0, 0, 0, 0, 0, 0};
-        if (next_tile < G) {
-            stage_tile<V, MODE, T>(a, stages + (s ^ 1) * Sh::STAGE, &bar[s ^ 1], nxt.r0, nxt.r1, nxt.k0, nxt.k1, pol);
-            if (after_tile < G) aft = load_bounds<MODE>(a, after_tile);
-        }
-
-        const bool ok = mbar_wait_bounded(&bar[s], (phases >> s) & 1u, kWaitLimitNs);
-        phases ^= 1u << s;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(a.err, static_cast<int>(LB_ERR_TIMEOUT));
-            if (next_tile < G) mbar_wait_bounded(&bar[s ^ 1], (phases >> (s ^ 1)) & 1u, kWaitLimitNs);
-            return;
-        }
-
-        if (!tile_ok<T>(cur.r0, cur.r1, cur.k0, cur.k1)) {
-            if (tid == 0) {
-                atomicExch(a.err, static_cast<int>(LB_ERR_BAD_MATRIX));
-                a.carry_row[tile] = a.num_rows;  // the fixup skips it
-                a.carry_val[tile] = 0.f;
+    if (warp < GW) {
+        // ---------------------------------------------------------------- gather warps
+        for (int i = 0; i < n_my; ++i) {
+            const int s = i % NS, b = i & 1;
+            bool ok = mbar_wait_bounded(&bars->full[s], (i / NS) & 1, kWaitLimitNs);
+            if (ok && i >= 2) ok = mbar_wait_bounded(&bars->pfree[b], ((i - 2) >> 1) & 1, kWaitLimitNs);
+            if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
+                if (lane == 0) atomicExch(a.err, static_cast<int>(LB_ERR_TIMEOUT));
+                return;
             }
-        } else {
-        const int nr = cur.r1 - cur.r0;
-        const int nk = cur.k1 - cur.k0;
-        const int k0 = cur.k0;
-        const TileSegs segs = tile_segs<V, MODE>(a, cur.r0, cur.r1, cur.k0, cur.k1);
-        const int *s_re = reinterpret_cast<const int *>(stage + segs.re.first);
-        const int *s_idx = reinterpret_cast<const int *>(stage + segs.idx.first);
-        float *s_y = s_out;
-        float *s_p = s_out + nr;
-
-        // 1. Products of the tile's atoms, all of a thread's gathers in flight at once.
-        {
-            int col[IPT];
-            float vv[IPT];
-#pragma unroll
-            for (int u = 0; u < IPT; ++u) {
-                const int j = tid + u * THREADS;
-                col[u] = 0;
-                vv[u] = 0.f;
-                if (j < nk) {
-                    col[u] = s_idx[j];
-                    if (MODE == kTransposed) {
-                        const int p = reinterpret_cast<const int *>(stage + segs.val.first)[j];
-                        vv[u] = to_f32(__ldg(static_cast<const V *>(a.val) + p));
-                    } else {
-                        vv[u] = to_f32(reinterpret_cast<const V *>(stage + segs.val.first)[j]);
-                    }
-                    if (MODE == kBatched) col[u] += batched_col_base(a, cur.m0, cur.m1, k0 + j);
-                }
-            }
-            float xv[IPT];
-#pragma unroll
-            for (int u = 0; u < IPT; ++u) {
-                const int j = tid + u * THREADS;
-                xv[u] = (j < nk) ? __ldg(a.x + col[u]) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < IPT; ++u) {
-                const int j = tid + u * THREADS;
-                if (j < nk) s_p[j] = vv[u] * xv[u];
-            }
-        }
-        __syncthreads();
-
-        // 2. Thread-level merge path inside the tile: find this thread's start on diagonal
-        //    d0, then consume its items (row ends close a row, nonzeros accumulate).
-        const int items = nr + nk;
-        const int d0 = min(tid * IPT, items);
-        const int d1 = min(d0 + IPT, items);
-        int lo = max(0, d0 - nk), hi = min(d0, nr);
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (mid + (s_re[mid] - k0) < d0)
-                lo = mid + 1;
+            const StageHdr h = hdrs[s];
+            float prod[IPT];
+            if (h.ok)
+                gather_products<V, IPT, MODE>(a, stages + s * Sh::STAGE, h, tid, prod);
             else
-                hi = mid;
-        }
-        int i = lo, j = d0 - lo;
-        float acc = 0.f, head = 0.f;
-        int head_row = -1;
 #pragma unroll
-        for (int q = 0; q < IPT; ++q) {
-            if (d0 + q < d1) {
-                if (i < nr && s_re[i] - k0 <= j) {
-                    if (head_row < 0) {
-                        head = acc;
-                        head_row = i;
-                    } else {
-                        s_y[i] = acc;
+                for (int q = 0; q < IPT; ++q) prod[q] = 0.f;
+            // The stage's indices and values are no longer needed once the products exist.
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->gdone[s]);
+            float *s_p = s_p0 + b * Sh::P_FLOATS;
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4)
+                *reinterpret_cast<float4 *>(s_p + ppad(tid * IPT + q)) =
+                    make_float4(prod[q], prod[q + 1], prod[q + 2], prod[q + 3]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->pready[b]);
+        }
+    } else if (warp < GW + Sh::SW) {
+        // ---------------------------------------------------------------- scan warps
+        const int st = tid - Sh::GT;  // scan thread index
+        const int sw = st >> 5;
+        for (int i = 0; i < n_my; ++i) {
+            const int s = i % NS, b = i & 1;
+            bool ok = mbar_wait_bounded(&bars->pready[b], (i >> 1) & 1, kWaitLimitNs);
+            if (ok) ok = mbar_wait_bounded(&bars->full[s], (i / NS) & 1, kWaitLimitNs);
+            StageHdr h;
+            h.ok = 0;
+            if (ok) {
+                h = hdrs[s];
+                if (h.ok) {
+                    // Row starts: row r0 + r + 1 starts at item s_re[r] - k0.
+                    const int nr = h.r1 - h.r0, nk = h.k1 - h.k0, lead = tile_lead(h);
+                    const int *s_re = reinterpret_cast<const int *>(stages + s * Sh::STAGE + h.re_first);
+                    for (int r = st; r < nr; r += Sh::ST) {
+                        const int p = s_re[r] - h.k0;
+                        if (p > 0 && p < nk) {
+                            const int sl = p + lead;
+                            atomicOr(&s_bits[sl >> 5], 1u << (sl & 31));
+                        }
                     }
-                    acc = 0.f;
-                    ++i;
-                } else {
-                    acc += s_p[j];
-                    ++j;
                 }
             }
-        }
-
-        // 3. Block-wide segmented scan of (ends a row?, partial after the last row end): a
-        //    thread's first completed row receives the partials of the threads before it back
-        //    to the last one that ended a row.
-        int fi = head_row >= 0;
-        float vi = acc;
+            if (scan_bar_any<Sh::ST>(!ok)) {  // every scan warp leaves together
+                if (st == 0) atomicExch(a.err, static_cast<int>(LB_ERR_TIMEOUT));
+                return;
+            }
+            const int tile = tile_of(i);
+            if (!h.ok) {
+                if (st == 0) {
+                    atomicExch(a.err, static_cast<int>(LB_ERR_BAD_MATRIX));
+                    a.carry_row[tile] = a.num_rows;  // the fixup skips it
+                    a.carry_val[tile] = 0.f;
+                }
+            } else {
+                const int nr = h.r1 - h.r0;
+                const int nk = h.k1 - h.k0;
+                const int k0 = h.k0;
+                const int lead = tile_lead(h);
+                const int *s_re = reinterpret_cast<const int *>(stages + s * Sh::STAGE + h.re_first);
+                float *s_p = s_p0 + b * Sh::P_FLOATS;
+                // Blocked segmented scan over SIPT slots per thread.
+                const int base = st * SIPT;
+                float v[SIPT];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const float vu = __shfl_up_sync(0xffffffffu, vi, off);
-            const int fu = __shfl_up_sync(0xffffffffu, fi, off);
-            if (lane >= off) {
-                if (!fi) vi = vu + vi;
-                fi |= fu;
+                for (int q = 0; q < SIPT; q += 4) {
+                    const float4 t4 = *reinterpret_cast<const float4 *>(s_p + ppad(base + q));
+                    v[q] = t4.x;
+                    v[q + 1] = t4.y;
+                    v[q + 2] = t4.z;
+                    v[q + 3] = t4.w;
+                }
+                const uint32_t flags = (s_bits[base >> 5] >> (base & 31)) & ((1u << SIPT) - 1u);
+#pragma unroll
+                for (int q = 1; q < SIPT; ++q)
+                    if (!((flags >> q) & 1u)) v[q] += v[q - 1];
+                int fi = flags != 0u;
+                float vi = v[SIPT - 1];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const float vu = __shfl_up_sync(0xffffffffu, vi, off);
+                    const int fu = __shfl_up_sync(0xffffffffu, fi, off);
+                    if (lane >= off) {
+                        if (!fi) vi = vu + vi;
+                        fi |= fu;
+                    }
+                }
+                if (lane == 31) {
+                    s_wf[sw] = fi;
+                    s_wv[sw] = vi;
+                }
+                scan_bar<Sh::ST>();
+                float pv = 0.f;
+#pragma unroll
+                for (int w = 0; w < Sh::SW; ++w) {
+                    if (w < sw) {
+                        const int fw = s_wf[w];
+                        const float vw = s_wv[w];
+                        pv = fw ? vw : pv + vw;
+                    }
+                }
+                float ve = __shfl_up_sync(0xffffffffu, vi, 1);
+                int fe = __shfl_up_sync(0xffffffffu, fi, 1);
+                if (lane == 0) {
+                    ve = 0.f;
+                    fe = 0;
+                }
+                const float carry_in = fe ? ve : pv + ve;
+                // Slots before this thread's first segment start continue the open segment.
+                const int first_flag = flags ? __ffs(flags) - 1 : SIPT;
+#pragma unroll
+                for (int q = 0; q < SIPT; ++q)
+                    if (q < first_flag) v[q] = carry_in + v[q];
+#pragma unroll
+                for (int q = 0; q < SIPT; q += 4)
+                    *reinterpret_cast<float4 *>(s_p + ppad(base + q)) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                scan_bar<Sh::ST>();
+                // Row sums: the scan value at each row's last nonzero in the tile.
+                for (int r = st; r < nr; r += Sh::ST) {
+                    const int end = s_re[r] - k0;
+                    const int start = r > 0 ? s_re[r - 1] - k0 : 0;
+                    a.y[h.r0 + r] = end > start ? s_p[ppad(end - 1 + lead)] : 0.f;
+                }
+                if (st == Sh::ST - 1) {
+                    const int open_start = nr > 0 ? s_re[nr - 1] - k0 : 0;
+                    a.carry_row[tile] = h.r1;
+                    a.carry_val[tile] = nk > open_start ? s_p[ppad(nk - 1 + lead)] : 0.f;
+                }
+                for (int w = st; w < Sh::BITS_WORDS; w += Sh::ST) s_bits[w] = 0u;
+            }
+            scan_bar<Sh::ST>();  // buffer, stage and bits are free
+            if (st == 0) {
+                mbar_arrive(&bars->pfree[b]);
+                mbar_arrive(&bars->sdone[s]);
             }
         }
-        if (lane == 31) {
-            s_wf[warp] = fi;
-            s_wv[warp] = vi;
+    } else {
+        // ---------------------------------------------------------------- producer warp
+        const uint64_t pol = policy_evict_first();
+        TileBounds nb = load_bounds<MODE>(a, tile_of(0));
+        for (int j = 0; j < n_my; ++j) {
+            const int s = j % NS;
+            const TileBounds cur = nb;
+            if (j + 1 < n_my) nb = load_bounds<MODE>(a, tile_of(j + 1));
+            if (j >= NS) {
+                const uint32_t par = ((j - NS) / NS) & 1;
+                bool ok = mbar_wait_bounded(&bars->gdone[s], par, kWaitLimitNs);
+                if (ok) ok = mbar_wait_bounded(&bars->sdone[s], par, kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) atomicExch(a.err, static_cast<int>(LB_ERR_TIMEOUT));
+                    return;
+                }
+            }
+            produce_tile<V, MODE, Sh::TILE_ITEMS>(a, &bars->full[s], &hdrs[s], stages + s * Sh::STAGE, cur, pol);
         }
-        __syncthreads();
-        float pv = 0.f;
-        for (int w = 0; w < warp; ++w) {
-            const int fw = s_wf[w];
-            const float vw = s_wv[w];
-            pv = fw ? vw : pv + vw;
-        }
-        float ve = __shfl_up_sync(0xffffffffu, vi, 1);
-        int fe = __shfl_up_sync(0xffffffffu, fi, 1);
-        if (lane == 0) {
-            ve = 0.f;
-            fe = 0;
-        }
-        if (head_row >= 0) s_y[head_row] = head + (fe ? ve : pv + ve);
-        if (tid == THREADS - 1) {
-            a.carry_row[tile] = cur.r1;
-            a.carry_val[tile] = fi ? vi : pv + vi;
-        }
-        __syncthreads();
-
-        // 4. Completed rows of the tile, coalesced.
-        for (int r = tid; r < nr; r += THREADS) a.y[cur.r0 + r] = s_y[r];
-        }
-
-        tile = next_tile;
-        cur = nxt;
-        next_tile = after_tile;
-        nxt = aft;
-        fence_proxy_async_smem();
-        __syncthreads();
     }
 }
 
 // Resident CTAs per SM of one kernel instance on the current device (computed once per
 // device; also raises the kernel's dynamic shared-memory limit).
-template <typename V, int THREADS, int IPT, int MODE>
+template <typename V, int GW, int IPT, int MODE>
 int merge_blocks_per_sm() {
-    using Sh = MergeShape<THREADS, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
     constexpr int kMaxDev = 64;
     static int cache[kMaxDev] = {0};
     static std::mutex mu;
@@ -389,40 +673,40 @@ int merge_blocks_per_sm() {
     if (cache[dev] > 0) return cache[dev];
     std::lock_guard<std::mutex> lock(mu);
     if (cache[dev] == 0) {
-        auto kern = merge_spmv_kernel<V, THREADS, IPT, MODE>;
+        auto kern = merge_spmv_kernel<V, GW, IPT, MODE>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Sh::SMEM)) !=
             cudaSuccess)
             return 0;
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, THREADS, Sh::SMEM) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Sh::THREADS, Sh::SMEM) != cudaSuccess) return 0;
         cache[dev] = nb > 0 ? nb : 1;
     }
     return cache[dev];
 }
 
-template <typename V, int THREADS, int IPT, int MODE>
+template <typename V, int GW, int IPT, int MODE>
 cudaError_t launch_merge_cfg(const MergeArgs &a, cudaStream_t st, cudaEvent_t eb, cudaEvent_t ea) {
-    using Sh = MergeShape<THREADS, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
-    const int per_sm = merge_blocks_per_sm<V, THREADS, IPT, MODE>();
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
+    const int per_sm = merge_blocks_per_sm<V, GW, IPT, MODE>();
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const long long wave = static_cast<long long>(per_sm) * current_sm_count();
     const int grid = static_cast<int>(a.num_tiles < wave ? a.num_tiles : wave);
     if (eb) cudaEventRecord(eb, st);
-    merge_spmv_kernel<V, THREADS, IPT, MODE><<<grid, THREADS, Sh::SMEM, st>>>(a);
+    merge_spmv_kernel<V, GW, IPT, MODE><<<grid, Sh::THREADS, Sh::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (ea) cudaEventRecord(ea, st);
     if (e != cudaSuccess) return e;
     return launch_fixup(a.num_tiles, a.num_rows, a.carry_row, a.carry_val, a.y, st);
 }
 
-// The (threads, items per thread) shapes compiled into the library.
-#define LB_MERGE_SHAPES(X) X(128, 8) X(256, 4) X(256, 8) X(256, 12) X(256, 16) X(512, 8)
+// The (gather threads, items per thread) shapes compiled into the library.
+#define LB_MERGE_SHAPES(X) X(128, 16) X(256, 8) X(256, 12) X(256, 16) X(384, 8) X(512, 8)
 
 template <typename V, int MODE>
 cudaError_t dispatch_merge_shape(int threads, int ipt, const MergeArgs &a, cudaStream_t st, cudaEvent_t eb,
                                  cudaEvent_t ea) {
 #define LB_TRY_SHAPE(TH, IP) \
-    if (threads == TH && ipt == IP) return launch_merge_cfg<V, TH, IP, MODE>(a, st, eb, ea);
+    if (threads == TH && ipt == IP) return launch_merge_cfg<V, TH / 32, IP, MODE>(a, st, eb, ea);
     LB_MERGE_SHAPES(LB_TRY_SHAPE)
 #undef LB_TRY_SHAPE
     return cudaErrorInvalidValue;

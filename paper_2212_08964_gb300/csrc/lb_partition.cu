@@ -36,11 +36,17 @@ __global__ void __launch_bounds__(256) partition_kernel(int m, long long W, int 
          base += warps * 32) {
         const long long r = base + lane;
         long long c_lo = 0, n_c = 0;
+        // Each lane loads offsets[r+1]; offsets[r] comes from the lane below (lane 0 loads it).
+        const int end_off = (r < m) ? __ldg(offsets + r + 1) : 0;
+        int start_off = __shfl_up_sync(0xffffffffu, end_off, 1);
+        if (lane == 0 && r > 0 && r <= m) start_off = __ldg(offsets + r);
         if (r <= m) {
-            const long long k_prev = (r == 0) ? -1 : (r - 1) + static_cast<long long>(__ldg(offsets + r));
-            const long long k_cur = (r == m) ? W : r + static_cast<long long>(__ldg(offsets + r + 1));
-            c_lo = k_prev + 1 > 0 ? (k_prev + 1 + T - 1) / T : 0;
-            long long c_hi = (r == m) ? G : k_cur / T;
+            // Merge positions fit 32 bits (m + nnz < 2^32): 32-bit division, not 64-bit.
+            const long long k_prev = (r == 0) ? -1 : (r - 1) + static_cast<long long>(start_off);
+            const long long k_cur = (r == m) ? W : r + static_cast<long long>(end_off);
+            const unsigned Tu = static_cast<unsigned>(T);
+            c_lo = k_prev + 1 > 0 ? (static_cast<unsigned>(k_prev) + Tu) / Tu : 0;
+            long long c_hi = (r == m) ? G : static_cast<unsigned>(k_cur) / Tu;
             if (c_hi > G) c_hi = G;  // only malformed offsets get here; keep writes in [0, G]
             n_c = c_hi >= c_lo ? c_hi - c_lo + 1 : 0;
         }
@@ -83,9 +89,8 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
     const long long W = static_cast<long long>(m) + nnz;
     const long long G = (W + tile_items - 1) / tile_items;
     const long long threads_needed = (static_cast<long long>(m) + 1 + 31) / 32 * 32;
-    long long blocks = (threads_needed + 255) / 256;
-    const long long cap = static_cast<long long>(current_sm_count()) * 16;
-    if (blocks > cap) blocks = cap;
+    long long blocks = (threads_needed + 255) / 256;  // one warp per 32 rows: latency, not bandwidth, is the limit
+    if (blocks > (1ll << 30)) blocks = 1ll << 30;
     if (blocks < 1) blocks = 1;
     partition_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(m, W, tile_items, G, offsets, tile_row, tile_nz);
     return cudaGetLastError();

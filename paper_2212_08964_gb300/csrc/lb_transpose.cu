@@ -9,6 +9,8 @@
 // digits, per-block digit counts, one exclusive scan over (digit, block), then a scatter in
 // which every element's rank among equal digits of its block comes from warp match masks.
 // Every step is a pure function of its input, so the plan is bit-exact and deterministic.
+#include <cstdlib>
+
 #include "lb_internal.cuh"
 
 namespace lb {
@@ -193,8 +195,10 @@ __global__ void gather_kernel(const int *src, const int *idx, int *dst, int n) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Per-nonzero maps over the forward merge-path partition: each tile stages its row ends and
-// finds the row of nonzero k as r0 + #{rows of the tile whose end offset is <= k}.
+// Per-nonzero maps over the forward merge-path partition.  Each tile stages its row ends;
+// each thread finds the row of its first nonzero by one binary search and walks forward over
+// its IPT consecutive nonzeros (row ends are sorted), recording row ids in shared memory;
+// a second, coalesced pass reads the column indices and writes the outputs.
 
 template <int THREADS, int IPT, bool ROWID>
 __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__restrict__ tile_row,
@@ -205,27 +209,41 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                                                             int *__restrict__ rowid) {
     constexpr int T = THREADS * IPT;
     __shared__ int s_re[T];
+    __shared__ int s_row[T];
     for (int tile = blockIdx.x; tile < G; tile += gridDim.x) {
         const int r0 = __ldg(tile_row + tile), r1 = __ldg(tile_row + tile + 1);
         const int k0 = __ldg(tile_nz + tile), k1 = __ldg(tile_nz + tile + 1);
         const int nr = r1 - r0, nk = k1 - k0;
         if (nr < 0 || nk < 0 || nr > T || nk > T) continue;  // malformed offsets (block-uniform)
-        for (int r = threadIdx.x; r < nr; r += THREADS) s_re[r] = __ldg(row_end + r0 + r);
+        for (int r = threadIdx.x; r < nr; r += THREADS) s_re[r] = __ldg(row_end + r0 + r) - k0;
+        __syncthreads();
+        const int base = threadIdx.x * IPT;
+        if (base < nk) {
+            int lo = 0, hi = nr;  // rows of the tile ending at or before `base`
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_re[mid] <= base)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            int i = lo;
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int j = base + q;
+                if (j < nk) {
+                    while (i < nr && s_re[i] <= j) ++i;
+                    s_row[j] = i;
+                }
+            }
+        }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < IPT; ++u) {
             const int j = threadIdx.x + u * THREADS;
             if (j < nk) {
                 const int k = k0 + j;
-                int lo = 0, hi = nr;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_re[mid] <= k)
-                        lo = mid + 1;
-                    else
-                        hi = mid;
-                }
-                const int row = r0 + lo;
+                const int row = r0 + s_row[j];
                 if (ROWID)
                     rowid[k] = row;
                 else
@@ -242,7 +260,7 @@ static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, 
                                     int *rowid, cudaStream_t st) {
     if (G <= 0) return cudaSuccess;
     int grid = G;
-    const int cap = current_sm_count() * 8;
+    const int cap = current_sm_count() * 6;
     if (grid > cap) grid = cap;
     // The staged row ends must fit: a tile holds at most tile_items rows.
     if (tile_items <= 1024)
@@ -323,6 +341,91 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
 done:
     cudaError_t e2 = cudaFreeAsync(work, st);
     return e != cudaSuccess ? e : e2;
+}
+
+// ------------------------------------------------------------------------------------------
+// Bringing CSR-ordered values into CSC order, every call, without random HBM reads.
+//
+// The transposed product needs, for CSC entry p, the value of CSR entry perm[p]: a random
+// permutation of an array far larger than L2.  Gathering it directly costs one DRAM sector
+// per nonzero.  Instead the CSC entries are cut into buckets of 2^shift consecutive entries
+// (each bucket's values fit comfortably in L2), and each call (1) streams the values once in
+// CSR order into bucket order -- CSR entries of one bucket keep their CSR order, so every
+// bucket receives one sequential stream of writes -- and (2) lets the transposed kernel
+// gather from the bucket being worked on, which stays resident in L2 while the persistent
+// CTAs sweep through it.  Both maps are fixed per structure, so results stay deterministic.
+
+int value_bucket_shift(long long nnz) {
+    int shift = 23;  // 8M entries: 32 MB of FP32 values
+    // LBSPMV_VALUE_BUCKET_SHIFT (8..30) overrides the bucket size, so tests can exercise
+    // many buckets on small matrices.
+    if (const char *env = getenv("LBSPMV_VALUE_BUCKET_SHIFT")) {
+        const int v = atoi(env);
+        if (v >= 8 && v <= 30) shift = v;
+    }
+    while (shift < 30 && ((nnz + (1ll << shift) - 1) >> shift) > 256) ++shift;
+    return shift;
+}
+
+__global__ void scatter_inverse_kernel(const int *src, int *dst, int n) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        dst[src[i]] = static_cast<int>(i);
+}
+
+cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket_pos, int *bucket_perm,
+                                cudaStream_t st) {
+    if (nnz <= 0) return cudaSuccess;
+    cudaError_t e;
+    const int nblocks = (nnz + kRsTile - 1) / kRsTile;
+    const long long hist_n = 256ll * nblocks;
+    const size_t ints = 3 * static_cast<size_t>(nnz) + static_cast<size_t>(hist_n) +
+                        static_cast<size_t>(scan_scratch_ints(hist_n));
+    int *work = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&work), ints * sizeof(int), st)) != cudaSuccess) return e;
+    int *pinv = work;              // CSR entry -> CSC position
+    int *keys_out = pinv + nnz;    // unused sorted keys
+    int *order = keys_out + nnz;   // bucket order -> CSR entry
+    int *hist = order + nnz;
+    int *sums = hist + hist_n;
+    const int grid = current_sm_count() * 8;
+    scatter_inverse_kernel<<<grid, 256, 0, st>>>(perm, pinv, nnz);
+    // One stable counting pass on the bucket number pinv >> shift (< 256 buckets).
+    radix_hist_kernel<<<nblocks, kRsThreads, 0, st>>>(pinv, nnz, shift, nblocks, hist);
+    if ((e = cudaGetLastError()) == cudaSuccess) e = exclusive_scan(hist, hist, hist_n, sums, st);
+    if (e == cudaSuccess) {
+        radix_scatter_kernel<<<nblocks, kRsThreads, 0, st>>>(pinv, nullptr, keys_out, order, nnz, shift, nblocks, hist);
+        scatter_inverse_kernel<<<grid, 256, 0, st>>>(order, bucket_pos, nnz);  // bucket_pos[order[q]] = q
+        gather_kernel<<<grid, 256, 0, st>>>(bucket_pos, perm, bucket_perm, nnz);  // bucket_perm[p] = bucket_pos[perm[p]]
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(work, st);
+    return e != cudaSuccess ? e : e2;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) bucket_values_kernel(int nnz, const E *__restrict__ v,
+                                                            const int *__restrict__ pos, E *__restrict__ tmp) {
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < nnz;
+         k += static_cast<long long>(gridDim.x) * blockDim.x)
+        tmp[__ldg(pos + k)] = __ldg(v + k);
+}
+
+cudaError_t launch_bucket_values(int nnz, int elem_bytes, const void *values, const int *bucket_pos, void *tmp,
+                                 cudaStream_t st) {
+    if (nnz <= 0) return cudaSuccess;
+    long long blocks = (static_cast<long long>(nnz) + 255) / 256;
+    const long long cap = static_cast<long long>(current_sm_count()) * 32;
+    if (blocks > cap) blocks = cap;
+    if (elem_bytes == 4)
+        bucket_values_kernel<int><<<static_cast<int>(blocks), 256, 0, st>>>(nnz, static_cast<const int *>(values),
+                                                                          bucket_pos, static_cast<int *>(tmp));
+    else if (elem_bytes == 2)
+        bucket_values_kernel<unsigned short><<<static_cast<int>(blocks), 256, 0, st>>>(
+            nnz, static_cast<const unsigned short *>(values), bucket_pos, static_cast<unsigned short *>(tmp));
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace lb

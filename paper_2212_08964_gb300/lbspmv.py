@@ -53,7 +53,7 @@ SCHEDULES = {
 }
 _SCHED_NAMES = {v: k for k, v in SCHEDULES.items()}
 # (threads, items per thread) shapes of the merge-path kernel compiled into the library.
-MERGE_SHAPES = [(128, 8), (256, 4), (256, 8), (256, 12), (256, 16), (512, 8)]
+MERGE_SHAPES = [(128, 16), (256, 8), (256, 12), (256, 16), (384, 8), (512, 8)]
 
 _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
 
@@ -92,6 +92,7 @@ def _declare(lib):
         "lb_spmv_dvalues": [_P, _P, _P, _P, _P, _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
+        "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
         "lb_spmv_batched": [_P, _P, _P, _I, _P, _P, _P],
         "lb_validate_csr": [_I, _I, _I, _P, _P, _I, _P, _P],
         "lb_device_error": [ctypes.POINTER(_I), _I],
@@ -319,6 +320,11 @@ class BatchedPlan:
                                        ctypes.byref(self._h)),
             "lb_batched_plan_create",
         )
+
+    def info(self) -> dict:
+        t, g, ti = _Tuning(), _I(), _I()
+        _check(_lib.lb_batched_plan_info(self._h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(ti)), "lb_batched_plan_info")
+        return {"threads": t.threads, "items_per_thread": t.items_per_thread, "num_tiles": g.value, "tile_items": ti.value}
 
     def partition(self):
         g = _I()

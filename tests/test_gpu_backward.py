@@ -143,3 +143,22 @@ def test_full_size_powerlaw_4m_backward(lb, orc):
     mx, med = check_bound(dx.cpu().numpy(), ref_dx, orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n), TOL32, "columns")
     print(f"powerlaw_4m dx: max rel err {mx:.3e} median {med:.3e}")
     assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+
+
+def test_bucketed_value_permutation(lb, orc, monkeypatch):
+    """Small value buckets (2^10 CSC entries) force the bucketed path on a small matrix."""
+    monkeypatch.setenv("LBSPMV_VALUE_BUCKET_SHIFT", "10")
+    a = workload("powerlaw_4k")
+    for dtype in (torch.float32, torch.bfloat16, torch.float16):
+        plan, ci, v = _plan_with_t(lb, a, dtype=dtype)
+        g = vec(a.m, 205)
+        dx1 = plan.spmv_t(v, dev(g))
+        dx2 = plan.spmv_t(v, dev(g))
+        torch.cuda.synchronize()
+        assert torch.equal(dx1, dx2)
+        vals = a.values if dtype == torch.float32 else rounded(a.values, dtype)
+        ref = orc.spmv_t(a.row_offsets, a.col_idx, vals, g, a.n)
+        check_bound(dx1.cpu().numpy(), ref, orc.col_absdot(a.row_offsets, a.col_idx, vals, g, a.n), TOL32, "columns")
+        co, ri, perm = plan.transpose()
+        oco, ori, operm = orc.transpose(a.row_offsets, a.col_idx, a.n)
+        assert np.array_equal(perm, operm) and np.array_equal(ri, ori)

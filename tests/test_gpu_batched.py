@@ -40,13 +40,15 @@ def _plan(lb, b, **tune):
     return lb.BatchedPlan(b.ms, b.ns, b.nnzs, dev(b.row_offsets), **tune)
 
 
-@pytest.mark.parametrize("shape", [(256, 8), (128, 8), (256, 16)])
+@pytest.mark.parametrize("shape", [(256, 8), (128, 16), (512, 8)])
 def test_batched_partition_bit_exact(lb, orc, shape):
     b = _batch_with_degenerates()
     plan = _plan(lb, b, threads=shape[0], items_per_thread=shape[1])
     tr, tn = plan.partition()
     ro_g = orc.block_diagonal_offsets(b.ms, b.nnzs, b.row_offsets)
-    otr, otn = orc.partition(ro_g, shape[0] * shape[1])
+    T = plan.info()["tile_items"]
+    assert T == shape[0] * shape[1] - 8
+    otr, otn = orc.partition(ro_g, T)
     assert np.array_equal(tr, otr) and np.array_equal(tn, otn)
 
 
@@ -100,5 +102,5 @@ def test_full_size_batched_4096(lb, orc):
     print(f"batched_4096: max rel err {mx:.3e} median {med:.3e}")
     ro_g = orc.block_diagonal_offsets(b.ms, b.nnzs, b.row_offsets)
     tr, tn = plan.partition()
-    otr, otn = orc.partition(ro_g, 2048)
+    otr, otn = orc.partition(ro_g, plan.info()["tile_items"])
     assert np.array_equal(tr, otr) and np.array_equal(tn, otn)

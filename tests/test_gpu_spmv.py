@@ -36,7 +36,7 @@ def test_worked_example_exact(lb):
         assert np.array_equal(y, f["y"]), sched
 
 
-@pytest.mark.parametrize("shape", [(128, 8), (256, 4), (256, 8), (256, 12), (256, 16), (512, 8)])
+@pytest.mark.parametrize("shape", [(128, 16), (256, 8), (256, 12), (256, 16), (384, 8), (512, 8)])
 def test_merge_path_shapes_powerlaw_4k(lb, orc, shape):
     a = workload("powerlaw_4k")
     x = vec(a.n, 101)
@@ -98,7 +98,7 @@ def test_long_rows_spanning_many_tiles(lb, orc):
     a = synth.csr_from_row_lengths(rng, n, lengths)
     x = vec(n, 104)
     ref, scale = _ref(orc, a, x)
-    for shape in [(256, 8), (128, 8), (512, 8)]:
+    for shape in [(256, 8), (128, 16), (512, 8)]:
         y, plan = _run(lb, a, x, "merge_path", threads=shape[0], items_per_thread=shape[1])
         assert plan.info()["num_tiles"] > 100
         check_bound(y, ref, scale, TOL32)
