@@ -62,8 +62,8 @@ typedef enum {
 typedef enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 } lb_dtype;
 
 /* Launch shape of a schedule; 0 selects the default.
- *   merge-path:   (threads, items_per_thread) in {(128, 16), (256, 8), (256, 12), (256, 16),
- *                 (384, 8), (512, 8)}, default (256, 8).  `threads` counts the gather threads
+ *   merge-path:   (threads, items_per_thread) in {(128, 16), (256, 8), (256, 16), (384, 8),
+ *                 (512, 8)}, default (256, 8).  `threads` counts the gather threads
  *                 of a CTA (scan and producer warps are added); one tile holds
  *                 threads * items_per_thread - 8 work items (rows + nonzeros);
  *   block-mapped: threads in {128, 256} (the group is the block);

@@ -40,7 +40,7 @@ int *device_error_word() {
 }
 
 bool merge_shape_ok(int threads, int ipt) {
-    static const int shapes[][2] = {{128, 16}, {256, 8}, {256, 12}, {256, 16}, {384, 8}, {512, 8}};
+    static const int shapes[][2] = {{128, 16}, {256, 8}, {256, 16}, {384, 8}, {512, 8}};
     for (const auto &s : shapes)
         if (s[0] == threads && s[1] == ipt) return true;
     return false;

@@ -46,32 +46,44 @@ namespace lb {
 // Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.
 template <int GW, int IPT, int SV>
 struct MergeShape {
-    static_assert(IPT % 4 == 0, "items per thread must be a multiple of 4 (128-bit shared loads)");
+    static_assert(IPT == 8 || IPT == 16, "items per thread: 8 or 16 (one byte or halfword of flags)");
     static constexpr int GT = GW * 32;   // gather threads
     static constexpr int T = GT * IPT;   // slots per tile
     // Work items per tile: a tile's first nonzero sits up to 7 slots past a 16-byte boundary,
     // so 8 slots are kept free for that lead.
     static constexpr int TILE_ITEMS = T - 8;
-    static constexpr int SIPT = 16;      // scan slots per scan thread
-    static_assert(T % (SIPT * 32) == 0, "tile must split into whole scan warps");
-    static constexpr int SW = T / (SIPT * 32);  // scan warps
-    static constexpr int ST = SW * 32;          // scan threads
+    static constexpr int SW = 4;                  // scan warps
+    static constexpr int ST = SW * 32;            // scan threads
+    static constexpr int GPS = GT / ST;           // gather threads per scan thread
     static constexpr int THREADS = GT + ST + 32;  // + one producer warp
     static constexpr int NSTAGE = 3;
     // One stage: row ends (4 B per row), indices (4 B per atom), values or CSR positions
     // (SV B per atom), each padded to 16 B at both ends.  rows + atoms <= T.
     static constexpr int STAGE = ((4 + SV) * T + 128 + 127) / 128 * 128;
-    static constexpr int BITS_WORDS = T / 32 + 2;
-    static constexpr int P_FLOATS = T + (T / 32) * 4;  // products with 4 floats of padding per 32
+    static constexpr int P_FLOATS = T + (T / 32) * 4;  // slot values with 4 floats of padding per 32
     static constexpr int HDR = 512;                    // mbarriers + stage headers
-    static constexpr size_t SMEM = HDR + NSTAGE * static_cast<size_t>(STAGE) + 2 * static_cast<size_t>(P_FLOATS) * 4 +
-                                   BITS_WORDS * 4 + 2 * 32 * 4;
+    // Row-start bits of each gather warp's slots (IPT words per warp, private to the warp).
+    static constexpr size_t BITS = (static_cast<size_t>(GW) * IPT * 4 + 127) / 128 * 128;
+    // Per product buffer: slot values, and per gather thread its aggregate, first-segment-start
+    // position and carry-in.  Buffers start 128-byte aligned (accessed as float4).
+    static constexpr size_t BUF = (static_cast<size_t>(P_FLOATS) * 4 + 3 * GT * 4 + 127) / 128 * 128;
+    static_assert((P_FLOATS * 4) % 16 == 0, "slot values must keep 16-byte alignment");
+    static constexpr size_t SMEM = HDR + NSTAGE * static_cast<size_t>(STAGE) + BITS + 2 * BUF;
     // Resident CTAs per SM from shared memory (228 KB per SM, 1 KB reserved per CTA), capped
     // by a register budget of 56 per thread.
     static constexpr int BY_SMEM = static_cast<int>((228 * 1024) / (SMEM + 1024));
     static constexpr int BY_REGS = 65536 / (THREADS * 56);
     static constexpr int MIN_BLOCKS_RAW = BY_SMEM < BY_REGS ? BY_SMEM : BY_REGS;
     static constexpr int MIN_BLOCKS = MIN_BLOCKS_RAW < 1 ? 1 : MIN_BLOCKS_RAW;
+};
+
+// One product buffer in shared memory.
+template <int GT>
+struct ProdBuf {
+    float *val;  // inclusive segmented scan of each gather thread's own slots (padded)
+    float *agg;  // per gather thread: sum after its last segment start (or of all its slots)
+    int *ff;     // per gather thread: first slot (0..IPT-1) starting a segment, IPT if none
+    float *cin;  // per gather thread: carry into its first segment
 };
 
 // Index of slot j in a padded product buffer: 4 floats of padding after every 32 keep the
@@ -325,23 +337,21 @@ __device__ __forceinline__ float half_bits_to_f32(unsigned short bits) {
 // g owns slots [g*IPT, (g+1)*IPT).  Slots outside [lead, lead + nk) are padding with product 0.
 __device__ __forceinline__ int tile_lead(const StageHdr &h) { return static_cast<int>(h.idx_first & 15u) >> 2; }
 
-// Products of gather thread g's slots of one tile (indices and values by vector shared loads,
-// all gathers in flight before the first use).
+// Gather thread g's slots of one tile: values in vv, gathers x[col] issued into xv (indices and
+// values by vector shared loads; the products are formed after other work by the caller).
 template <typename V, int IPT, int MODE>
-__device__ __forceinline__ void gather_products(const MergeArgs &a, const unsigned char *stage, const StageHdr &h, int g,
-                                                float (&prod)[IPT]) {
+__device__ __forceinline__ void gather_issue(const MergeArgs &a, const unsigned char *stage, const StageHdr &h, int g,
+                                             float (&vv)[IPT], float (&xv)[IPT]) {
     const int nk = h.k1 - h.k0;
     const int lead = tile_lead(h);
     const int slot0 = g * IPT;
     const int item0 = slot0 - lead;  // tile item of this thread's first slot
-    float vv[IPT], xv[IPT];
     int col[IPT];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         col[q] = 0;
         vv[q] = 0.f;
         xv[q] = 0.f;
-        prod[q] = 0.f;
     }
     if (item0 + IPT <= 0 || item0 >= nk) return;  // nothing of the tile in this thread's slots
     const unsigned char *idx0 = stage + h.idx_first - lead * 4;  // slot 0, 16-byte aligned
@@ -428,27 +438,72 @@ __device__ __forceinline__ void gather_products(const MergeArgs &a, const unsign
             xv[q] = __ldg(a.x + c);
         }
     }
-#pragma unroll
-    for (int q = 0; q < IPT; ++q) prod[q] = vv[q] * xv[q];
 }
 
-// Named barrier over the scan warps only (id 1).
-template <int NTHREADS>
-__device__ __forceinline__ void scan_bar() {
-    asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
+// Row-start bits of one gather warp's 32 * IPT slots of a tile, built by the warp alone from
+// the staged row ends (row r0 + r + 1 starts at slot s_re[r] - k0 + lead; slots are
+// non-decreasing in r): a 32-way lower-bound search for the first row start in the warp's
+// slots, then the row starts in range OR-ed into the warp's private bit words.  Returns this
+// lane's IPT bits and leaves the words cleared.
+template <int IPT>
+__device__ __forceinline__ uint32_t warp_row_start_flags(const unsigned char *stage, const StageHdr &h, int gwarp,
+                                                         uint32_t *wbits) {
+    const int lane = threadIdx.x & 31;
+    const int S0 = gwarp * 32 * IPT;
+    const int nr = h.r1 - h.r0, nk = h.k1 - h.k0, lead = tile_lead(h);
+    const int *s_re = reinterpret_cast<const int *>(stage + h.re_first);
+    const int lo_slot = S0 > lead + 1 ? S0 : lead + 1;        // item 0 starts no segment
+    const int hi_slot = (S0 + 32 * IPT) < (nk + lead) ? (S0 + 32 * IPT) : (nk + lead);  // exclusive
+    auto slot_of = [&](int r) { return s_re[r] - h.k0 + lead; };
+    int lo = 0, hi = nr;  // first r with slot_of(r) >= lo_slot lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) >> 5;
+        const int q = lo + lane * step;
+        const int cnt = __popc(__ballot_sync(0xffffffffu, q < hi && slot_of(q) < lo_slot));
+        const int nlo = cnt > 0 ? lo + (cnt - 1) * step + 1 : lo;
+        const int nhi = lo + cnt * step < hi ? lo + cnt * step : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    {
+        const int q = lo + lane;
+        lo += __popc(__ballot_sync(0xffffffffu, q < hi && slot_of(q) < lo_slot));
+    }
+    if (lo_slot < hi_slot) {
+        for (int rb = lo;; rb += 32) {
+            const int r = rb + lane;
+            const int sl = r < nr ? slot_of(r) : 0x40000000;
+            const bool in = sl < hi_slot;
+            if (in) atomicOr(&wbits[(sl - S0) >> 5], 1u << ((sl - S0) & 31));
+            if (!__shfl_sync(0xffffffffu, static_cast<int>(in), 31)) break;
+        }
+    }
+    __syncwarp();
+    const uint32_t mine = (IPT == 8) ? static_cast<uint32_t>(reinterpret_cast<const unsigned char *>(wbits)[lane])
+                                     : static_cast<uint32_t>(reinterpret_cast<const unsigned short *>(wbits)[lane]);
+    __syncwarp();
+    if (lane < IPT) wbits[lane] = 0u;
+    __syncwarp();
+    return mine;
 }
 
-// The same barrier with an OR vote, so the scan warps take the same branch.
-template <int NTHREADS>
-__device__ __forceinline__ bool scan_bar_any(bool pred) {
+// Named barriers: id 1 over the scan warps, id 2 over the gather warps.
+template <int ID, int NTHREADS>
+__device__ __forceinline__ void group_bar() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NTHREADS) : "memory");
+}
+
+// The same barrier with an OR vote, so a group takes the same branch.
+template <int ID, int NTHREADS>
+__device__ __forceinline__ bool group_bar_any(bool pred) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"(static_cast<uint32_t>(pred)), "n"(NTHREADS)
+        : "r"(static_cast<uint32_t>(pred)), "n"(ID), "n"(NTHREADS)
         : "memory");
     return r != 0;
 }
@@ -459,15 +514,22 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
     merge_spmv_kernel(const MergeArgs a) {
     using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
     constexpr int NS = Sh::NSTAGE;
-    constexpr int SIPT = Sh::SIPT;
+    constexpr int GT = Sh::GT;
     extern __shared__ __align__(128) unsigned char smem[];
     Bars *bars = reinterpret_cast<Bars *>(smem);
     StageHdr *hdrs = reinterpret_cast<StageHdr *>(smem + 256);
     unsigned char *stages = smem + Sh::HDR;
-    float *s_p0 = reinterpret_cast<float *>(stages + NS * Sh::STAGE);  // product buffers (x2)
-    uint32_t *s_bits = reinterpret_cast<uint32_t *>(s_p0 + 2 * Sh::P_FLOATS);  // segment starts by slot
-    int *s_wf = reinterpret_cast<int *>(s_bits + Sh::BITS_WORDS);
-    float *s_wv = reinterpret_cast<float *>(s_wf + 32);
+    uint32_t *wbits_all = reinterpret_cast<uint32_t *>(stages + NS * Sh::STAGE);  // per gather warp
+    unsigned char *bufmem = stages + NS * Sh::STAGE + Sh::BITS;
+    auto buf = [&](int b) {
+        unsigned char *p = bufmem + b * Sh::BUF;
+        ProdBuf<GT> pb;
+        pb.val = reinterpret_cast<float *>(p);
+        pb.agg = pb.val + Sh::P_FLOATS;
+        pb.ff = reinterpret_cast<int *>(pb.agg + GT);
+        pb.cin = reinterpret_cast<float *>(pb.ff + GT);
+        return pb;
+    };
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -489,11 +551,15 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
         }
         mbar_fence_init();
     }
-    for (int w = tid; w < Sh::BITS_WORDS; w += Sh::THREADS) s_bits[w] = 0u;
+    for (int w = tid; w < static_cast<int>(Sh::BITS / 4); w += Sh::THREADS) wbits_all[w] = 0u;
     __syncthreads();
 
     if (warp < GW) {
         // ---------------------------------------------------------------- gather warps
+        // Per tile: products of this thread's IPT slots, the scan of those slots restarting at
+        // row starts, and the thread's aggregate for the scan warps.  No barrier: each warp
+        // runs at its own pace.
+        const int g = tid;
         for (int i = 0; i < n_my; ++i) {
             const int s = i % NS, b = i & 1;
             bool ok = mbar_wait_bounded(&bars->full[s], (i / NS) & 1, kWaitLimitNs);
@@ -503,52 +569,101 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
                 return;
             }
             const StageHdr h = hdrs[s];
-            float prod[IPT];
-            if (h.ok)
-                gather_products<V, IPT, MODE>(a, stages + s * Sh::STAGE, h, tid, prod);
-            else
+            const ProdBuf<GT> pb = buf(b);
+            float vv[IPT], xv[IPT];
+            uint32_t flags = 0;
+            if (h.ok) {
+                // Gathers first; the row-start bits are found while they are in flight.
+                gather_issue<V, IPT, MODE>(a, stages + s * Sh::STAGE, h, g, vv, xv);
+                flags = warp_row_start_flags<IPT>(stages + s * Sh::STAGE, h, warp, wbits_all + warp * IPT);
+            } else {
 #pragma unroll
-                for (int q = 0; q < IPT; ++q) prod[q] = 0.f;
-            // The stage's indices and values are no longer needed once the products exist.
+                for (int q = 0; q < IPT; ++q) vv[q] = xv[q] = 0.f;
+            }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars->gdone[s]);
-            float *s_p = s_p0 + b * Sh::P_FLOATS;
+            if (lane == 0) mbar_arrive(&bars->gdone[s]);  // the stage is no longer read here
+            float v[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) v[q] = vv[q] * xv[q];
+#pragma unroll
+            for (int q = 1; q < IPT; ++q)
+                if (!((flags >> q) & 1u)) v[q] += v[q - 1];
 #pragma unroll
             for (int q = 0; q < IPT; q += 4)
-                *reinterpret_cast<float4 *>(s_p + ppad(tid * IPT + q)) =
-                    make_float4(prod[q], prod[q + 1], prod[q + 2], prod[q + 3]);
+                *reinterpret_cast<float4 *>(pb.val + ppad(g * IPT + q)) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            pb.agg[g] = v[IPT - 1];
+            pb.ff[g] = flags ? __ffs(flags) - 1 : IPT;
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars->pready[b]);
         }
     } else if (warp < GW + Sh::SW) {
         // ---------------------------------------------------------------- scan warps
-        const int st = tid - Sh::GT;  // scan thread index
-        const int sw = st >> 5;
+        // Per tile: the first scan warp scans the gather threads' aggregates (the carry into
+        // each thread's first segment); then every scan warp reads rows' sums at their last
+        // nonzero, and the last thread writes the tile's carry.
+        constexpr int ST = Sh::ST;
+        constexpr int PER = GT / 32;  // aggregates per lane of the first scan warp
+        static_assert(PER % 4 == 0, "aggregates are read four at a time");
+        const int st = tid - GT;
         for (int i = 0; i < n_my; ++i) {
             const int s = i % NS, b = i & 1;
             bool ok = mbar_wait_bounded(&bars->pready[b], (i >> 1) & 1, kWaitLimitNs);
             if (ok) ok = mbar_wait_bounded(&bars->full[s], (i / NS) & 1, kWaitLimitNs);
-            StageHdr h;
-            h.ok = 0;
-            if (ok) {
-                h = hdrs[s];
-                if (h.ok) {
-                    // Row starts: row r0 + r + 1 starts at item s_re[r] - k0.
-                    const int nr = h.r1 - h.r0, nk = h.k1 - h.k0, lead = tile_lead(h);
-                    const int *s_re = reinterpret_cast<const int *>(stages + s * Sh::STAGE + h.re_first);
-                    for (int r = st; r < nr; r += Sh::ST) {
-                        const int p = s_re[r] - h.k0;
-                        if (p > 0 && p < nk) {
-                            const int sl = p + lead;
-                            atomicOr(&s_bits[sl >> 5], 1u << (sl & 31));
-                        }
+            const ProdBuf<GT> pb = buf(b);
+            if (ok && st < 32) {
+                int fl[PER];
+                float ag[PER];
+#pragma unroll
+                for (int q = 0; q < PER; q += 4) {
+                    const int4 f4 = *reinterpret_cast<const int4 *>(pb.ff + st * PER + q);
+                    const float4 a4 = *reinterpret_cast<const float4 *>(pb.agg + st * PER + q);
+                    fl[q] = f4.x < IPT;
+                    fl[q + 1] = f4.y < IPT;
+                    fl[q + 2] = f4.z < IPT;
+                    fl[q + 3] = f4.w < IPT;
+                    ag[q] = a4.x;
+                    ag[q + 1] = a4.y;
+                    ag[q + 2] = a4.z;
+                    ag[q + 3] = a4.w;
+                }
+                int fi = fl[0];
+                float vi = ag[0];
+#pragma unroll
+                for (int q = 1; q < PER; ++q) {
+                    vi = fl[q] ? ag[q] : vi + ag[q];
+                    fi |= fl[q];
+                }
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const float vu = __shfl_up_sync(0xffffffffu, vi, off);
+                    const int fu = __shfl_up_sync(0xffffffffu, fi, off);
+                    if (lane >= off) {
+                        if (!fi) vi = vu + vi;
+                        fi |= fu;
                     }
                 }
+                float ve = __shfl_up_sync(0xffffffffu, vi, 1);
+                int fe = __shfl_up_sync(0xffffffffu, fi, 1);
+                if (lane == 0) {
+                    ve = 0.f;
+                    fe = 0;
+                }
+                float c = ve;  // carry into gather thread st*PER (a single warp: no earlier warps)
+                float cin[PER];
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    cin[q] = c;
+                    c = fl[q] ? ag[q] : c + ag[q];
+                }
+#pragma unroll
+                for (int q = 0; q < PER; q += 4)
+                    *reinterpret_cast<float4 *>(pb.cin + st * PER + q) = make_float4(cin[q], cin[q + 1], cin[q + 2], cin[q + 3]);
             }
-            if (scan_bar_any<Sh::ST>(!ok)) {  // every scan warp leaves together
+            if (group_bar_any<1, ST>(!ok)) {  // the scan warps leave together
                 if (st == 0) atomicExch(a.err, static_cast<int>(LB_ERR_TIMEOUT));
                 return;
             }
+            const StageHdr h = hdrs[s];
             const int tile = tile_of(i);
             if (!h.ok) {
                 if (st == 0) {
@@ -562,77 +677,25 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
                 const int k0 = h.k0;
                 const int lead = tile_lead(h);
                 const int *s_re = reinterpret_cast<const int *>(stages + s * Sh::STAGE + h.re_first);
-                float *s_p = s_p0 + b * Sh::P_FLOATS;
-                // Blocked segmented scan over SIPT slots per thread.
-                const int base = st * SIPT;
-                float v[SIPT];
-#pragma unroll
-                for (int q = 0; q < SIPT; q += 4) {
-                    const float4 t4 = *reinterpret_cast<const float4 *>(s_p + ppad(base + q));
-                    v[q] = t4.x;
-                    v[q + 1] = t4.y;
-                    v[q + 2] = t4.z;
-                    v[q + 3] = t4.w;
-                }
-                const uint32_t flags = (s_bits[base >> 5] >> (base & 31)) & ((1u << SIPT) - 1u);
-#pragma unroll
-                for (int q = 1; q < SIPT; ++q)
-                    if (!((flags >> q) & 1u)) v[q] += v[q - 1];
-                int fi = flags != 0u;
-                float vi = v[SIPT - 1];
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const float vu = __shfl_up_sync(0xffffffffu, vi, off);
-                    const int fu = __shfl_up_sync(0xffffffffu, fi, off);
-                    if (lane >= off) {
-                        if (!fi) vi = vu + vi;
-                        fi |= fu;
-                    }
-                }
-                if (lane == 31) {
-                    s_wf[sw] = fi;
-                    s_wv[sw] = vi;
-                }
-                scan_bar<Sh::ST>();
-                float pv = 0.f;
-#pragma unroll
-                for (int w = 0; w < Sh::SW; ++w) {
-                    if (w < sw) {
-                        const int fw = s_wf[w];
-                        const float vw = s_wv[w];
-                        pv = fw ? vw : pv + vw;
-                    }
-                }
-                float ve = __shfl_up_sync(0xffffffffu, vi, 1);
-                int fe = __shfl_up_sync(0xffffffffu, fi, 1);
-                if (lane == 0) {
-                    ve = 0.f;
-                    fe = 0;
-                }
-                const float carry_in = fe ? ve : pv + ve;
-                // Slots before this thread's first segment start continue the open segment.
-                const int first_flag = flags ? __ffs(flags) - 1 : SIPT;
-#pragma unroll
-                for (int q = 0; q < SIPT; ++q)
-                    if (q < first_flag) v[q] = carry_in + v[q];
-#pragma unroll
-                for (int q = 0; q < SIPT; q += 4)
-                    *reinterpret_cast<float4 *>(s_p + ppad(base + q)) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-                scan_bar<Sh::ST>();
-                // Row sums: the scan value at each row's last nonzero in the tile.
-                for (int r = st; r < nr; r += Sh::ST) {
+                // Scan value at slot e: the owner's own inclusive value, plus the carry into the
+                // owner when e lies before the owner's first segment start.
+                auto value_at = [&](int e) {
+                    const int owner = e / IPT;
+                    const float v = pb.val[ppad(e)];
+                    return (e - owner * IPT) < pb.ff[owner] ? pb.cin[owner] + v : v;
+                };
+                for (int r = st; r < nr; r += ST) {
                     const int end = s_re[r] - k0;
                     const int start = r > 0 ? s_re[r - 1] - k0 : 0;
-                    a.y[h.r0 + r] = end > start ? s_p[ppad(end - 1 + lead)] : 0.f;
+                    a.y[h.r0 + r] = end > start ? value_at(end - 1 + lead) : 0.f;
                 }
-                if (st == Sh::ST - 1) {
+                if (st == ST - 1) {
                     const int open_start = nr > 0 ? s_re[nr - 1] - k0 : 0;
                     a.carry_row[tile] = h.r1;
-                    a.carry_val[tile] = nk > open_start ? s_p[ppad(nk - 1 + lead)] : 0.f;
+                    a.carry_val[tile] = nk > open_start ? value_at(nk - 1 + lead) : 0.f;
                 }
-                for (int w = st; w < Sh::BITS_WORDS; w += Sh::ST) s_bits[w] = 0u;
             }
-            scan_bar<Sh::ST>();  // buffer, stage and bits are free
+            group_bar<1, ST>();  // buffer and stage are free
             if (st == 0) {
                 mbar_arrive(&bars->pfree[b]);
                 mbar_arrive(&bars->sdone[s]);
@@ -700,7 +763,7 @@ cudaError_t launch_merge_cfg(const MergeArgs &a, cudaStream_t st, cudaEvent_t eb
 }
 
 // The (gather threads, items per thread) shapes compiled into the library.
-#define LB_MERGE_SHAPES(X) X(128, 16) X(256, 8) X(256, 12) X(256, 16) X(384, 8) X(512, 8)
+#define LB_MERGE_SHAPES(X) X(128, 16) X(256, 8) X(256, 16) X(384, 8) X(512, 8)
 
 template <typename V, int MODE>
 cudaError_t dispatch_merge_shape(int threads, int ipt, const MergeArgs &a, cudaStream_t st, cudaEvent_t eb,

@@ -53,7 +53,7 @@ SCHEDULES = {
 }
 _SCHED_NAMES = {v: k for k, v in SCHEDULES.items()}
 # (threads, items per thread) shapes of the merge-path kernel compiled into the library.
-MERGE_SHAPES = [(128, 16), (256, 8), (256, 12), (256, 16), (384, 8), (512, 8)]
+MERGE_SHAPES = [(128, 16), (256, 8), (256, 16), (384, 8), (512, 8)]
 
 _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
 

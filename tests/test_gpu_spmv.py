@@ -36,7 +36,7 @@ def test_worked_example_exact(lb):
         assert np.array_equal(y, f["y"]), sched
 
 
-@pytest.mark.parametrize("shape", [(128, 16), (256, 8), (256, 12), (256, 16), (384, 8), (512, 8)])
+@pytest.mark.parametrize("shape", [(128, 16), (256, 8), (256, 16), (384, 8), (512, 8)])
 def test_merge_path_shapes_powerlaw_4k(lb, orc, shape):
     a = workload("powerlaw_4k")
     x = vec(a.n, 101)
@@ -44,6 +44,18 @@ def test_merge_path_shapes_powerlaw_4k(lb, orc, shape):
     ref, scale = _ref(orc, a, x)
     mx, med = check_bound(y, ref, scale, TOL32)
     print(f"merge {shape}: max rel err {mx:.3e} median {med:.3e}")
+
+
+@pytest.mark.parametrize("shape", [(128, 16), (256, 8), (256, 16), (384, 8), (512, 8)])
+def test_merge_path_many_tiles_per_cta(lb, orc, shape):
+    """Enough tiles that every persistent CTA cycles through all stages and both product
+    buffers several times (the small matrices above give most CTAs a single tile)."""
+    a = synth.powerlaw_csr(300_000, 300_000, 6_000_000, 1.4, 50_000, seed=33)
+    x = vec(a.n, 110)
+    y, plan = _run(lb, a, x, "merge_path", threads=shape[0], items_per_thread=shape[1])
+    assert plan.info()["num_tiles"] > 1000  # several tiles for every resident CTA
+    ref, scale = _ref(orc, a, x)
+    check_bound(y, ref, scale, TOL32)
 
 
 @pytest.mark.parametrize("sched,tune", [
