@@ -47,7 +47,8 @@ typedef enum {
     LB_ERR_UNSUPPORTED = -3, /* valid request this build does not implement */
     LB_ERR_NO_MEMORY = -4,   /* a plan or workspace allocation failed */
     LB_ERR_CUDA = -5,        /* a CUDA runtime call failed */
-    LB_ERR_TIMEOUT = -6      /* a kernel gave up on a bounded wait (device error word) */
+    LB_ERR_TIMEOUT = -6,     /* a kernel gave up on a bounded wait (device error word) */
+    LB_ERR_TOO_LARGE = -7    /* the request exceeds a fixed-size static workspace */
 } lb_status;
 
 typedef enum {
@@ -93,6 +94,35 @@ int lb_version(void);
  */
 lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_idx,
                   const void *values, lb_dtype vdt, const float *x, float *y, cudaStream_t stream);
+
+/*
+ * lb_spmv_static: y = A x like lb_spmv, but with NO device allocation.  The dissertation has
+ * no counterpart; this is an interface for callers that must not allocate: a process whose
+ * device memory is already reserved by another allocator (a framework's caching allocator,
+ * or an arena sized to the card), where lb_spmv's cudaMallocAsync workspace can fail with
+ * out-of-memory; latency-bound loops where an allocation may block on the pool or driver; or
+ * code that has promised its host framework to allocate only through that framework.
+ *
+ * Schedule: always merge-path with the (256, 8) launch shape (tiles of
+ * LB_SPMV_STATIC_TILE_ITEMS work items), whatever the matrix size.
+ * Workspace: a file-scope __device__ array inside the library, one per device, holding the
+ * partition and carry arrays of at most LB_SPMV_STATIC_MAX_TILES tiles (about 1 MiB).  So
+ * m + nnz must be at most LB_SPMV_STATIC_MAX_TILES * LB_SPMV_STATIC_TILE_ITEMS
+ * (133,693,440); larger requests return LB_ERR_TOO_LARGE before any GPU work.
+ * Set-up: the FIRST call on each device (with that device current) looks up the array's
+ * device address (cudaGetSymbolAddress), caches it, and sets the merge-path kernel's
+ * shared-memory limit; make that first call before any stream capture.  Later calls only enqueue two small memsets (the carry arrays are cleared
+ * every call) and the partition, merge-path and fixup kernels on `stream`.
+ * Concurrency: every call on one device shares the one workspace, so calls that overlap in
+ * time (on different streams, or from several host threads without stream ordering between
+ * them) RACE and give wrong results.  Calls ordered on one stream are safe.
+ * Arguments, results and other errors are as for lb_spmv.
+ */
+#define LB_SPMV_STATIC_MAX_TILES 65536
+#define LB_SPMV_STATIC_TILE_ITEMS 2040
+lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offsets, const int *col_idx,
+                         const void *values, lb_dtype vdt, const float *x, float *y,
+                         cudaStream_t stream);
 
 /*
  * Merge-path partition (Alg. alg:work-oriented, "2DSearch"; Ch.4 Sec. "Merge-path load

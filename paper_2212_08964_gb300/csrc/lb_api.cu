@@ -131,6 +131,8 @@ cudaError_t dmalloc(P **p, size_t count) {
 
 }  // namespace
 
+int *lb::device_error_ptr() { return device_error_word(); }
+
 struct lb_plan {
     int device = -1;
     int m = 0, n = 0, nnz = 0;
@@ -208,6 +210,8 @@ const char *lb_status_string(lb_status s) {
             return "LB_ERR_CUDA: CUDA runtime error";
         case LB_ERR_TIMEOUT:
             return "LB_ERR_TIMEOUT: a kernel gave up on a bounded wait";
+        case LB_ERR_TOO_LARGE:
+            return "LB_ERR_TOO_LARGE: the matrix exceeds the fixed static workspace";
     }
     return "unknown lb_status";
 }

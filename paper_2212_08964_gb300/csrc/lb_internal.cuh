@@ -213,4 +213,7 @@ cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci,
 // Device properties of the current device (cached).
 int current_sm_count();
 
+// Device address of the current device's error word (looked up once per device), or nullptr.
+int *device_error_ptr();
+
 }  // namespace lb

@@ -25,6 +25,7 @@ __all__ = [
     "ensure_loaded",
     "library_path",
     "spmv",
+    "spmv_static",
     "partition",
     "num_tiles",
     "Plan",
@@ -42,6 +43,11 @@ LB_OK = 0
 LB_ERR_INVALID_ARG = -1
 LB_ERR_UNSUPPORTED = -3
 LB_ERR_TIMEOUT = -6
+LB_ERR_TOO_LARGE = -7
+# Fixed workspace of lb_spmv_static: tiles of STATIC_TILE_ITEMS work items, at most
+# STATIC_MAX_TILES of them (m + nnz <= STATIC_MAX_TILES * STATIC_TILE_ITEMS).
+STATIC_MAX_TILES = 65536
+STATIC_TILE_ITEMS = 2040
 
 SCHEDULES = {
     "auto": 0,
@@ -81,6 +87,7 @@ def _declare(lib):
     lib.lb_version.restype = _I
     sigs = {
         "lb_spmv": [_I, _I, _I, _P, _P, _P, _I, _P, _P, _P],
+        "lb_spmv_static": [_I, _I, _I, _P, _P, _P, _I, _P, _P, _P],
         "lb_partition": [_I, _I, _P, _I, _P, _P, _P],
         "lb_plan_create": [_I, _I, _I, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_plan_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -186,6 +193,28 @@ def spmv(row_offsets, col_idx, values, x, n: int | None = None, out=None, stream
         "lb_spmv",
     )
     return y
+
+
+def spmv_static(row_offsets, col_idx, values, x, out, n: int | None = None, stream=None) -> torch.Tensor:
+    """y = A x through lb_spmv_static: merge-path with the library's fixed static workspace,
+    no device allocation (the caller provides ``out``).  Calls that overlap in time on one
+    device race on that workspace; calls ordered on one stream are safe."""
+    lib = ensure_loaded()
+    m = row_offsets.numel() - 1
+    nnz = col_idx.numel()
+    n = x.numel() if n is None else n
+    _need(row_offsets, torch.int32, "row_offsets")
+    _need(col_idx, torch.int32, "col_idx")
+    _need(values, None, "values", nnz)
+    _need(x, torch.float32, "x", n)
+    _need(out, torch.float32, "out", m)
+    _check(
+        lib.lb_spmv_static(
+            m, n, nnz, _ptr(row_offsets), _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(out), _stream(stream)
+        ),
+        "lb_spmv_static",
+    )
+    return out
 
 
 def partition(row_offsets, nnz: int, tile_items: int, stream=None):
