@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -83,10 +84,15 @@ def measured_hbm_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the main kernel's source with comments and blank space removed, so a recorded
+    DRAM-traffic figure is used only while the code it was measured on is unchanged."""
     h = hashlib.sha256()
     for f in ("lb_merge.cuh", "lb_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2212_08964_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2212_08964_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -21,10 +21,13 @@
 //   * a producer warp moves each tile's row ends, indices and values into a shared-memory
 //     stage with 1-D bulk TMA copies (three stages in flight);
 //   * gather warps (GW) read their IPT consecutive slots of a staged tile with vector loads,
-//     gather x, and store the products into one of two product buffers;
-//   * scan warps (SW) mark row starts, scan the products in blocked order (IPT_S slots per
-//     thread, warp shuffles, one shared-memory step), write the finished rows to y with
-//     coalesced stores and the open row's partial sum as the tile's carry.
+//     issue the x gathers, build their slots' row-start bits from the staged row ends while
+//     the gathers are in flight, then scan their own products (restarting at row starts)
+//     into one of two product buffers, with one aggregate per thread;
+//   * scan warps (SW): the first scans the gather threads' aggregates into the carry into
+//     each thread's first row; then all of them read each finished row's sum at its last
+//     nonzero, write y with coalesced stores, and write the open row's partial sum as the
+//     tile's carry.
 // Stages and product buffers are recycled through "done" barriers, so no role waits for
 // another except when a buffer is genuinely empty or full.  Every wait is bounded: a kernel
 // that gives up records LB_ERR_TIMEOUT and returns.
