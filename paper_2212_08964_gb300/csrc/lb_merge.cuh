@@ -46,8 +46,10 @@
 
 namespace lb {
 
-// Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.
-template <int GW, int IPT, int SV>
+// Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.  SV is
+// the size of the third staged array (values, or CSR positions for the transposed product);
+// NS is the number of shared-memory stages.
+template <int GW, int IPT, int SV, int NS>
 struct MergeShape {
     static_assert(IPT == 8 || IPT == 16, "items per thread: 8 or 16 (one byte or halfword of flags)");
     static constexpr int GT = GW * 32;   // gather threads
@@ -59,7 +61,7 @@ struct MergeShape {
     static constexpr int ST = SW * 32;            // scan threads
     static constexpr int GPS = GT / ST;           // gather threads per scan thread
     static constexpr int THREADS = GT + ST + 32;  // + one producer warp
-    static constexpr int NSTAGE = 3;
+    static constexpr int NSTAGE = NS;
     // One stage: row ends (4 B per row), indices (4 B per atom), values or CSR positions
     // (SV B per atom), each padded to 16 B at both ends.  rows + atoms <= T.
     static constexpr int STAGE = ((4 + SV) * T + 128 + 127) / 128 * 128;
@@ -162,6 +164,11 @@ __device__ __forceinline__ Seg make_seg(const void *base, long long e_lo, long l
 template <typename V, int MODE>
 struct MergeTraits {
     static constexpr uint32_t SV = (MODE == kTransposed) ? 4u : static_cast<uint32_t>(sizeof(V));
+    // Stages: the transposed product keeps twice as many gathers in flight per thread (the
+    // value through its CSR position as well as g), and those need L1 capacity; two stages
+    // leave more of the SM's unified L1/shared memory to the L1 and measure faster for it,
+    // while the forward product measures faster with three.
+    static constexpr int NS = (MODE == kTransposed) ? 2 : 3;
     __device__ static const void *third(const MergeArgs &a) {
         return (MODE == kTransposed) ? static_cast<const void *>(a.perm) : a.val;
     }
@@ -512,11 +519,12 @@ __device__ __forceinline__ bool group_bar_any(bool pred) {
 }
 
 template <typename V, int GW, int IPT, int MODE>
-__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>::THREADS,
-                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>::MIN_BLOCKS)
+__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>::THREADS,
+                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>::MIN_BLOCKS)
     merge_spmv_kernel(const MergeArgs a) {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>;
     constexpr int NS = Sh::NSTAGE;
+    static_assert(NS <= static_cast<int>(sizeof(Bars::full) / sizeof(uint64_t)), "one barrier set per stage");
     constexpr int GT = Sh::GT;
     extern __shared__ __align__(128) unsigned char smem[];
     Bars *bars = reinterpret_cast<Bars *>(smem);
@@ -543,7 +551,7 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
     auto tile_of = [&](int i) { return static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x); };
 
     if (tid == 0) {
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < NS; ++q) {
             mbar_init(&bars->full[q], 1);
             mbar_init(&bars->gdone[q], GW);
             mbar_init(&bars->sdone[q], 1);
@@ -730,7 +738,7 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
 // device; also raises the kernel's dynamic shared-memory limit).
 template <typename V, int GW, int IPT, int MODE>
 int merge_blocks_per_sm() {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>;
     constexpr int kMaxDev = 64;
     static int cache[kMaxDev] = {0};
     static std::mutex mu;
@@ -752,7 +760,7 @@ int merge_blocks_per_sm() {
 
 template <typename V, int GW, int IPT, int MODE>
 cudaError_t launch_merge_cfg(const MergeArgs &a, cudaStream_t st, cudaEvent_t eb, cudaEvent_t ea) {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV)>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>;
     const int per_sm = merge_blocks_per_sm<V, GW, IPT, MODE>();
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const long long wave = static_cast<long long>(per_sm) * current_sm_count();
