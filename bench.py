@@ -1,12 +1,17 @@
 #!/usr/bin/env python
 """Benchmark: load-balanced CSR SpMV forward + backward on GB300.
 
-One step is one pass of the whole hot path over the large power-law matrix
-(m = n = 4,194,304, ~64M nonzeros, Pareto row lengths with exponent 1.3, rows up to 500k):
+One step is one training pass of y = A x (as the autograd function runs it) over the large
+power-law matrix (m = n = 4,194,304, ~64M nonzeros, Pareto row lengths with exponent 1.3,
+rows up to 500k), with the plan (merge-path partition, CSC view) built once per structure:
 
-  forward   y  = A x      lb_spmv: merge-path partition + persistent SpMV + carry fixup
-  backward  dx = A^T g    lb_spmv_t: merge-path over the CSC view (built once, outside timing)
-            dv = g . x    lb_spmv_dvalues: per-nonzero map over the forward partition
+  forward   y  = A x      lb_spmv_planned_save: persistent merge-path SpMV + carry fixup, also
+                          saving x[col] of every nonzero for the values gradient
+  backward  dx = A^T g    lb_spmv_t: value buckets + merge-path over the CSC view + fixup
+            dv = g . x    lb_spmv_dvalues_gathered: per-nonzero map over the forward partition
+
+The partition alone and the one-shot lb_spmv (partition + SpMV + fixup every call) are timed
+separately and reported under config.components_us.
 
 ``value`` is whole-job algorithmic GB/s: bytes = nnz*(value+index) + offsets + x + y for each
 of the three passes (counting every dense vector once), divided by the device time of the
@@ -37,7 +42,6 @@ METRIC = "CSR SpMV GB/s as % of GB300 HBM peak; fwd+bwd and batched vs plain"
 UNIT = "GB/s"
 WORKLOAD = "powerlaw_4m"
 FALLBACK_HBM_GBS = 6800.0
-MAIN_KERNEL = "merge_spmv_kernel (plain, FP32 values)"
 
 
 def parse_args(argv=None):
@@ -96,14 +100,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per launch of the main kernel from a committed ncu summary, if the kernel
-    source has not changed since it was captured; else None."""
+def recorded_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if the kernel source has
+    not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d.get(workload)
+        e = d.get(workload, {}).get(kernel)
         if e and e.get("kernel_source_hash") == kernel_source_hash():
             return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -317,26 +321,29 @@ def run_ours(args):
     y = torch.empty(a.m, device=dev)
     dx = torch.empty(a.n, device=dev)
     dv = torch.empty(a.nnz, device=dev)
+    xg = torch.empty(a.nnz, device=dev)
     plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
     plan.build_transpose(ci)
     info = plan.info()
     torch.cuda.synchronize()
 
     def step(vals, xx, gg):
-        lb.spmv(ro, ci, vals, xx, out=y)
+        # The training step of y = A x under autograd: forward (saving x[col] per nonzero for
+        # the values gradient), then dx = A^T g and dvalues = g[row] * x[col].
+        plan.spmv(ci, vals, xx, out=y, save_gathered=xg)
         plan.spmv_t(vals, gg, out=dx)
-        plan.dvalues(ci, gg, xx, out=dv)
+        plan.dvalues_gathered(gg, xg, out=dv)
 
-    launches_per_step = 3 + 2 + 1
-    fwd_b, bwd_b, dv_b = step_bytes(a.m, a.n, a.nnz)
-    total_b = fwd_b + bwd_b + dv_b
+    launches_per_step = 2 + 3 + 1
+    fwd_b, bwd_t_b, dv_b = step_bytes(a.m, a.n, a.nnz)
+    total_b = fwd_b + bwd_t_b + dv_b
 
     for _ in range(max(args.warmup, 3)):
         step(v, xd, gd)
     K = max(args.steps, 1)
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    for e in ev_b + ev_a:  # create the events before the timed region
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(K)]  # noqa: E731
+    evf_b, evf_a, evt_b, evt_a, evd_b, evd_a = mk(), mk(), mk(), mk(), mk(), mk()
+    for e in evf_b + evf_a + evt_b + evt_a + evd_b + evd_a:  # create the events before the timed region
         e.record()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -345,8 +352,16 @@ def run_ours(args):
     with ClockSampler(local) as clocks:
         t0.record()
         for i in range(K):
-            lb.set_profile_events(ev_b[i], ev_a[i])
-            step(v, xd, gd)
+            # The same step, with events around each pass's main kernel (recorded by the library
+            # on the launching stream for the merge-path kernels).
+            lb.set_profile_events(evf_b[i], evf_a[i])
+            plan.spmv(ci, v, xd, out=y, save_gathered=xg)
+            lb.set_profile_events(evt_b[i], evt_a[i])
+            plan.spmv_t(v, gd, out=dx)
+            lb.set_profile_events(None, None)
+            evd_b[i].record()
+            plan.dvalues_gathered(gd, xg, out=dv)
+            evd_a[i].record()
         t1.record()
         torch.cuda.synchronize()
     lb.set_profile_events(None, None)
@@ -354,12 +369,34 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / K
     ms_max = max_over_ranks(ms, world)
-    main_ms = float(np.mean([b.elapsed_time(e) for b, e in zip(ev_b, ev_a)]))
+    mean_ms = lambda b, e: float(np.mean([x.elapsed_time(y_) for x, y_ in zip(b, e)]))  # noqa: E731
+    kern = {
+        "merge_spmv_kernel<plain> (y = A x, saving x[col])": (mean_ms(evf_b, evf_a), fwd_b + 4 * a.nnz),
+        "merge_spmv_kernel<transposed> (dx = A^T g)": (mean_ms(evt_b, evt_a), bwd_t_b),
+        "tile_rows_kernel<dvalues from saved gathers>": (mean_ms(evd_b, evd_a), 8 * a.nnz + 4 * (a.m + 1) + 4 * a.m),
+    }
     assert lb.device_error() == 0
 
     peak, peak_kind = measured_hbm_peak()
-    achieved = fwd_b / (main_ms * 1e-3) / 1e9
+    kernels = {k: {"avg_launch_ms": t, "algorithmic_bytes_per_launch": b, "achieved_GBps": b / (t * 1e-3) / 1e9,
+                   "frac": b / (t * 1e-3) / 1e9 / peak} for k, (t, b) in kern.items()}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_b = kern[dom]
+    achieved = dom_b / (dom_ms * 1e-3) / 1e9
     value = total_b * world / (ms_max * 1e-3) / 1e9
+
+    # Components outside the timed step: the partition (once per structure in a plan) and the
+    # one-shot lb_spmv, which recomputes the partition on every call.
+    part_tr = torch.empty(info["num_tiles"] + 1, dtype=torch.int32, device=dev)
+    part_tn = torch.empty_like(part_tr)
+    comp = {
+        "partition_us": 1e3 * _time(torch, lambda: lb._lib.lb_partition(a.m, a.nnz, ro.data_ptr(), info["tile_items"],
+                                                                         part_tr.data_ptr(), part_tn.data_ptr(),
+                                                                         torch.cuda.current_stream().cuda_stream), 20),
+        "forward_oneshot_lb_spmv_us": 1e3 * _time(torch, lambda: lb.spmv(ro, ci, v, xd, out=y), 20),
+        "forward_planned_us": 1e3 * _time(torch, lambda: plan.spmv(ci, v, xd, out=y), 20),
+        "dvalues_gathering_x_us": 1e3 * _time(torch, lambda: plan.dvalues(ci, gd, xd, out=dv), 20),
+    }
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(args.warmup, 3),
@@ -369,14 +406,18 @@ def run_ours(args):
             "workload": f"{args.workload} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz,
             "schedule": info["schedule"], "threads": info["threads"], "items_per_thread": info["items_per_thread"],
             "num_tiles": info["num_tiles"], "parallelism": f"replicas x{world}",
+            "step": "plan built once per structure (partition, CSC view); per step: forward saving x[col], "
+                    "dx = A^T g, dvalues from the saved gathers",
             "l2": f"no flush: each step streams {total_b / 1e9:.2f} GB of inputs, above the 129 MB L2",
-            "bytes_per_step": {"forward": fwd_b, "backward_dx": bwd_b, "backward_dvalues": dv_b},
+            "bytes_per_step": {"forward": fwd_b, "backward_dx": bwd_t_b, "backward_dvalues": dv_b},
+            "components_us": comp,
         },
         "roofline": {
-            "bound": "hbm", "kernel": MAIN_KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": recorded_traffic(args.workload),
-            "algorithmic_bytes_per_launch": fwd_b, "avg_launch_ms": main_ms,
+            "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": recorded_traffic(args.workload, dom),
+            "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_ms,
         },
+        "kernels": kernels,
         "gpu_launches": launches_per_step * K,
         "clocks": clocks.summary(),
     }

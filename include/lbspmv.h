@@ -194,6 +194,24 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x,
                           float *dvalues, cudaStream_t stream);
 
+/*
+ * y = A x with a merge-path plan (as lb_spmv_planned), also saving the gathered operand of
+ * every nonzero: x_gathered[k] = x[col_idx[k]] (device, nnz floats, overwritten).  The values
+ * gradient dvalues[k] = g[row(k)] * x[col_idx[k]] needs exactly these, so
+ * lb_spmv_dvalues_gathered can form it by streaming them back instead of gathering x again.
+ * Costs 4 bytes per nonzero of coalesced stores.  LB_ERR_UNSUPPORTED for plans whose schedule
+ * is not merge-path.  No allocation, no synchronization.
+ */
+lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
+                               const float *x, float *y, float *x_gathered, cudaStream_t stream);
+
+/*
+ * dvalues[k] = g[row(k)] * x_gathered[k] with x_gathered from lb_spmv_planned_save (the same
+ * values as lb_spmv_dvalues, bit for bit); row(k) from the plan's forward partition.
+ */
+lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
+                                   cudaStream_t stream);
+
 void lb_plan_destroy(lb_plan *p);
 
 /*
@@ -246,9 +264,10 @@ lb_status lb_validate_csr(int m, int n, int nnz, const int *row_offsets, const i
 lb_status lb_device_error(int *status, int clear);
 
 /*
- * Profiling aid: while set (non-NULL), every merge-path SpMV call records `before` right
- * before and `after` right after its main kernel on the call's stream.  Process-wide, not
- * thread-safe; pass NULLs to stop.
+ * Profiling aid: while set (non-NULL), every merge-path SpMV call (lb_spmv, lb_spmv_planned,
+ * lb_spmv_planned_save, lb_spmv_t, lb_spmv_batched) records `before` right before and `after`
+ * right after its main kernel on the call's stream.  Process-wide, not thread-safe; pass
+ * NULLs to stop.
  */
 lb_status lb_set_profile_events(cudaEvent_t before, cudaEvent_t after);
 

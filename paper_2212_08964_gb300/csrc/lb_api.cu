@@ -387,6 +387,35 @@ lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *valu
                                        g_ev_after));
 }
 
+lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
+                               const float *x, float *y, float *x_gathered, cudaStream_t stream) {
+    if (!p || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
+    if (p->sched != LB_SCHED_MERGE_PATH) return LB_ERR_UNSUPPORTED;
+    if (p->m == 0) return LB_OK;
+    if (!y || (p->nnz > 0 && (!col_idx || !values || !x || !x_gathered))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(y, 0, static_cast<size_t>(p->m) * sizeof(float), stream));
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    MergeArgs a{};
+    a.num_tiles = p->G;
+    a.num_rows = p->m;
+    a.num_atoms = p->nnz;
+    a.tile_row = p->tile_row;
+    a.tile_nz = p->tile_nz;
+    a.row_end = p->ro + 1;
+    a.idx = col_idx;
+    a.val = values;
+    a.x = x;
+    a.y = y;
+    a.carry_row = p->carry_row;
+    a.carry_val = p->carry_val;
+    a.xg = x_gathered;
+    a.err = err;
+    return from_cuda(launch_merge_spmv(vdt, kPlain, p->tune.threads, p->tune.items_per_thread, a, stream, g_ev_before,
+                                       g_ev_after));
+}
+
 lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t stream) {
     if (!p) return LB_ERR_INVALID_ARG;
     if (p->nnz > 0 && !col_idx) return LB_ERR_INVALID_ARG;
@@ -494,7 +523,7 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
     a.err = err;
     const int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
     const int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
-    return from_cuda(launch_merge_spmv(vdt, kTransposed, threads, ipt, a, stream, nullptr, nullptr));
+    return from_cuda(launch_merge_spmv(vdt, kTransposed, threads, ipt, a, stream, g_ev_before, g_ev_after));
 }
 
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
@@ -503,8 +532,18 @@ lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, 
     if (p->nnz == 0) return LB_OK;
     if (!col_idx || !g || !x || !dvalues) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(
-        launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, dvalues, stream));
+    return from_cuda(launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, nullptr,
+                                    dvalues, stream));
+}
+
+lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
+                                   cudaStream_t stream) {
+    if (!p) return LB_ERR_INVALID_ARG;
+    if (p->nnz == 0) return LB_OK;
+    if (!g || !x_gathered || !dvalues) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    return from_cuda(launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, nullptr, g, nullptr,
+                                    x_gathered, dvalues, stream));
 }
 
 void lb_plan_destroy(lb_plan *p) {

@@ -146,6 +146,7 @@ struct MergeArgs {
     const int *mat_nz_base;   // batched: [K+1] first nonzero of each matrix
     const int *mat_col_base;  // batched: [K] offset of each matrix's x inside x_concat
     const int *tile_mat;      // batched: [G+1] matrix holding each tile's first nonzero
+    float *xg;                // plain only, may be null: xg[k] = x[idx[k]] is saved for every atom
     int *err;                 // device error word
 };
 
@@ -175,10 +176,11 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
 cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, const int *ro,
                           const int *ci, const void *v, const float *x, float *y, cudaStream_t stream);
 
-// dvalues over the forward partition.
+// dvalues over the forward partition: dv[k] = g[row(k)] * x[ci[k]], or, with xg non-null,
+// dv[k] = g[row(k)] * xg[k] from x gathers saved by the forward product (ci and x unused).
 cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
-                           cudaStream_t stream);
+                           const int *row_end, const int *ci, const float *g, const float *x, const float *xg,
+                           float *dv, cudaStream_t stream);
 
 // Stable CSR -> CSC transpose (deterministic LSD radix sort by column).
 struct TransposeOut {

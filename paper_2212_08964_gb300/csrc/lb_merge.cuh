@@ -450,6 +450,28 @@ __device__ __forceinline__ void gather_issue(const MergeArgs &a, const unsigned 
     }
 }
 
+// The forward product's saved gathers: xg[k] = x[col_idx[k]] for gather thread g's nonzeros
+// (streaming stores; 16-byte vector stores when the thread's slots are all nonzeros of the
+// tile and aligned).  The values gradient reads them back instead of gathering x again.
+template <int IPT>
+__device__ __forceinline__ void save_gathered(float *xg, const StageHdr &h, int g, const float (&xv)[IPT]) {
+    const int nk = h.k1 - h.k0;
+    const int item0 = g * IPT - tile_lead(h);
+    if (item0 + IPT <= 0 || item0 >= nk) return;
+    if (item0 >= 0 && item0 + IPT <= nk) {
+        float *dst = xg + h.k0 + item0;
+        if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4)
+                __stcs(reinterpret_cast<float4 *>(dst + q), make_float4(xv[q], xv[q + 1], xv[q + 2], xv[q + 3]));
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+        if (item0 + q >= 0 && item0 + q < nk) __stcs(xg + h.k0 + item0 + q, xv[q]);
+}
+
 // Row-start bits of one gather warp's 32 * IPT slots of a tile, built by the warp alone from
 // the staged row ends (row r0 + r + 1 starts at slot s_re[r] - k0 + lead; slots are
 // non-decreasing in r): a 32-way lower-bound search for the first row start in the warp's
@@ -596,6 +618,7 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
             float v[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) v[q] = vv[q] * xv[q];
+            if (MODE == kPlain && a.xg != nullptr && h.ok) save_gathered<IPT>(a.xg, h, g, xv);
 #pragma unroll
             for (int q = 1; q < IPT; ++q)
                 if (!((flags >> q) & 1u)) v[q] += v[q - 1];

@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                                                             const int *__restrict__ tile_nz,
                                                             const int *__restrict__ row_end,
                                                             const int *__restrict__ ci, const float *__restrict__ g,
-                                                            const float *__restrict__ x, float *__restrict__ dv,
-                                                            int *__restrict__ rowid) {
+                                                            const float *__restrict__ x, const float *__restrict__ xg,
+                                                            float *__restrict__ dv, int *__restrict__ rowid) {
     constexpr int T = THREADS * IPT;
     __shared__ int s_re[T];
     __shared__ int s_row[T];
@@ -246,6 +246,8 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                 const int row = r0 + s_row[j];
                 if (ROWID)
                     rowid[k] = row;
+                else if (xg != nullptr)
+                    __stcs(dv + k, __ldg(g + row) * __ldcs(xg + k));
                 else
                     dv[k] = __ldg(g + row) * __ldg(x + __ldg(ci + k));
             }
@@ -256,28 +258,28 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
 
 template <bool ROWID>
 static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, const int *tile_nz,
-                                    const int *row_end, const int *ci, const float *g, const float *x, float *dv,
-                                    int *rowid, cudaStream_t st) {
+                                    const int *row_end, const int *ci, const float *g, const float *x,
+                                    const float *xg, float *dv, int *rowid, cudaStream_t st) {
     if (G <= 0) return cudaSuccess;
     int grid = G;
     const int cap = current_sm_count() * 6;
     if (grid > cap) grid = cap;
     // The staged row ends must fit: a tile holds at most tile_items rows.
     if (tile_items <= 1024)
-        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
+        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, xg, dv, rowid);
     else if (tile_items <= 2048)
-        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
+        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, xg, dv, rowid);
     else if (tile_items <= 4096)
-        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
+        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, xg, dv, rowid);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
-                           cudaStream_t stream) {
-    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, dv, nullptr,
+                           const int *row_end, const int *ci, const float *g, const float *x, const float *xg,
+                           float *dv, cudaStream_t stream) {
+    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, xg, dv, nullptr,
                                    stream);
 }
 
@@ -313,7 +315,7 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
         cudaSuccess)
         goto done;
     if ((e = launch_tile_rows<true>(num_tiles, tile_items, tile_row, tile_nz, ro + 1, nullptr, nullptr, nullptr,
-                                    nullptr, rowid, st)) != cudaSuccess)
+                                    nullptr, nullptr, rowid, st)) != cudaSuccess)
         goto done;
     {
         int bits = 0;

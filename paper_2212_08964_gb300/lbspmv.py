@@ -97,6 +97,8 @@ def _declare(lib):
         "lb_plan_transpose": [_P, _P, _P, _P],
         "lb_spmv_t": [_P, _P, _I, _P, _P, _P],
         "lb_spmv_dvalues": [_P, _P, _P, _P, _P, _P],
+        "lb_spmv_planned_save": [_P, _P, _P, _I, _P, _P, _P, _P],
+        "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -271,14 +273,21 @@ class Plan:
         return tr, tn
 
     # -- forward
-    def spmv(self, col_idx, values, x, out=None, stream=None) -> torch.Tensor:
+    def spmv(self, col_idx, values, x, out=None, stream=None, save_gathered=None) -> torch.Tensor:
+        """y = A x.  With ``save_gathered`` (nnz float32), also x[col_idx[k]] for every nonzero
+        (lb_spmv_planned_save; merge-path plans), for ``dvalues_gathered``."""
         _need(col_idx, torch.int32, "col_idx", self.nnz)
         _need(values, None, "values", self.nnz)
         _need(x, torch.float32, "x", self.n)
         y = torch.empty(self.m, dtype=torch.float32, device=x.device) if out is None else out
         _need(y, torch.float32, "y", self.m)
-        _check(_lib.lb_spmv_planned(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y), _stream(stream)),
-               "lb_spmv_planned")
+        if save_gathered is None:
+            _check(_lib.lb_spmv_planned(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y),
+                                        _stream(stream)), "lb_spmv_planned")
+        else:
+            _need(save_gathered, torch.float32, "save_gathered", self.nnz)
+            _check(_lib.lb_spmv_planned_save(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y),
+                                             _ptr(save_gathered), _stream(stream)), "lb_spmv_planned_save")
         return y
 
     # -- backward
@@ -313,6 +322,16 @@ class Plan:
         dv = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if out is None else out
         _need(dv, torch.float32, "dvalues", self.nnz)
         _check(_lib.lb_spmv_dvalues(self._h, _ptr(col_idx), _ptr(g), _ptr(x), _ptr(dv), _stream(stream)), "lb_spmv_dvalues")
+        return dv
+
+    def dvalues_gathered(self, g, x_gathered, out=None, stream=None) -> torch.Tensor:
+        """dvalues[k] = g[row(k)] * x_gathered[k] (x gathers saved by ``spmv(save_gathered=...)``)."""
+        _need(g, torch.float32, "g", self.m)
+        _need(x_gathered, torch.float32, "x_gathered", self.nnz)
+        dv = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if out is None else out
+        _need(dv, torch.float32, "dvalues", self.nnz)
+        _check(_lib.lb_spmv_dvalues_gathered(self._h, _ptr(g), _ptr(x_gathered), _ptr(dv), _stream(stream)),
+               "lb_spmv_dvalues_gathered")
         return dv
 
     def close(self):
@@ -389,23 +408,28 @@ class SpMV(torch.autograd.Function):
     """y = A x with gradients for the values and for x.
 
     Backward: dx = A^T g by merge-path over the plan's CSC view (built on first use),
-    dvalues = g[row] * x[col] per nonzero over the forward partition.
+    dvalues = g[row] * x[col] per nonzero over the forward partition.  When the values need a
+    gradient and the plan is merge-path, the forward saves x[col] of every nonzero (4 bytes per
+    nonzero) and the backward streams them back instead of gathering x again.
     """
 
     @staticmethod
     def forward(ctx, values, x, plan: Plan, col_idx):
         ctx.plan = plan
-        ctx.save_for_backward(values, x, col_idx)
-        return plan.spmv(col_idx, values.detach(), x.detach())
+        xg = None
+        if ctx.needs_input_grad[0] and plan.info()["schedule"] == "merge_path":
+            xg = torch.empty(plan.nnz, dtype=torch.float32, device=x.device)
+        ctx.save_for_backward(values, x, col_idx, xg)
+        return plan.spmv(col_idx, values.detach(), x.detach(), save_gathered=xg)
 
     @staticmethod
     def backward(ctx, g):
-        values, x, col_idx = ctx.saved_tensors
+        values, x, col_idx, xg = ctx.saved_tensors
         plan = ctx.plan
         g = g.contiguous().float()
         dvals = dx = None
         if ctx.needs_input_grad[0]:
-            dvals = plan.dvalues(col_idx, g, x.detach())
+            dvals = plan.dvalues(col_idx, g, x.detach()) if xg is None else plan.dvalues_gathered(g, xg)
             if values.dtype != torch.float32:
                 dvals = dvals.to(values.dtype)
         if ctx.needs_input_grad[1]:

@@ -62,6 +62,50 @@ def test_spmv_t_and_dvalues(lb, orc, name, dtype):
     assert np.array_equal(dv.cpu().numpy(), dv_ref)
 
 
+@pytest.mark.parametrize("name", ["worked", "powerlaw_4k", "skew", "wide", "stencil_small"])
+@pytest.mark.parametrize("shape", [(256, 8), (128, 16), (512, 8)])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_saved_gathers(lb, orc, name, shape, dtype):
+    """The forward that saves x[col] per nonzero: y unchanged bit for bit, the saved gathers
+    equal x[col] exactly, and dvalues from them equal the oracle's products exactly."""
+    a = _cases()[name]
+    ro, ci, v = to_dev(a, dtype)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path", threads=shape[0], items_per_thread=shape[1])
+    x = vec(a.n, 205)
+    g = vec(a.m, 206)
+    xd = dev(x)
+    y0 = plan.spmv(ci, v, xd)
+    xg = torch.full((a.nnz,), float("nan"), device="cuda")
+    y1 = plan.spmv(ci, v, xd, save_gathered=xg)
+    dv = plan.dvalues_gathered(dev(g), xg)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    assert np.array_equal(xg.cpu().numpy(), x[a.col_idx])
+    dv_ref = orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32)
+    assert np.array_equal(dv.cpu().numpy(), dv_ref)
+
+
+def test_saved_gathers_unaligned_views(lb, orc):
+    """Column indices and the saved-gather buffer at element offsets 1..3 (16-byte alignment
+    differs between them), through the scalar-store path."""
+    a = workload("powerlaw_4k")
+    x = vec(a.n, 207)
+    g = vec(a.m, 208)
+    for off_c, off_g in [(1, 0), (0, 3), (2, 1), (3, 3)]:
+        ci_buf = torch.zeros(a.nnz + 4, dtype=torch.int32, device="cuda")
+        ci_buf[off_c: off_c + a.nnz] = dev(a.col_idx)
+        ci = ci_buf[off_c: off_c + a.nnz]
+        xg_buf = torch.full((a.nnz + 4,), float("nan"), device="cuda")
+        xg = xg_buf[off_g: off_g + a.nnz]
+        plan = lb.Plan(dev(a.row_offsets), a.n, a.nnz, schedule="merge_path")
+        plan.spmv(ci, dev(a.values), dev(x), save_gathered=xg)
+        dv = plan.dvalues_gathered(dev(g), xg)
+        torch.cuda.synchronize()
+        assert np.array_equal(xg.cpu().numpy(), x[a.col_idx])
+        assert torch.isnan(xg_buf[:off_g]).all() and torch.isnan(xg_buf[off_g + a.nnz:]).all()
+        assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+
+
 @pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped"])
 def test_autograd_function(lb, orc, sched):
     a = workload("powerlaw_4k")
@@ -136,13 +180,20 @@ def test_full_size_powerlaw_4m_backward(lb, orc):
     plan, ci, v = _plan_with_t(lb, a)
     x = vec(a.n, 1)
     g = vec(a.m, 3)
+    xg = torch.empty(a.nnz, device="cuda")
+    y = plan.spmv(ci, v, dev(x), save_gathered=xg)
     dx = plan.spmv_t(v, dev(g))
-    dv = plan.dvalues(ci, dev(g), dev(x))
+    dv = plan.dvalues_gathered(dev(g), xg)
+    dv2 = plan.dvalues(ci, dev(g), dev(x))
     torch.cuda.synchronize()
+    ref_y = orc.spmv(a.row_offsets, a.col_idx, a.values, x)
+    check_bound(y.cpu().numpy(), ref_y, orc.row_absdot(a.row_offsets, a.col_idx, a.values, x), TOL32)
     ref_dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
     mx, med = check_bound(dx.cpu().numpy(), ref_dx, orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n), TOL32, "columns")
     print(f"powerlaw_4m dx: max rel err {mx:.3e} median {med:.3e}")
-    assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+    dv_ref = orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32)
+    assert np.array_equal(dv.cpu().numpy(), dv_ref)
+    assert torch.equal(dv, dv2)
 
 
 def test_bucketed_value_permutation(lb, orc, monkeypatch):
