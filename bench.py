@@ -373,7 +373,7 @@ def run_ours(args):
     kern = {
         "merge_spmv_kernel<plain> (y = A x, saving x[col])": (mean_ms(evf_b, evf_a), fwd_b + 4 * a.nnz),
         "merge_spmv_kernel<transposed> (dx = A^T g)": (mean_ms(evt_b, evt_a), bwd_t_b),
-        "tile_rows_kernel<dvalues from saved gathers>": (mean_ms(evd_b, evd_a), 8 * a.nnz + 4 * (a.m + 1) + 4 * a.m),
+        "dvalues_saved_kernel (dvalues from the saved gathers)": (mean_ms(evd_b, evd_a), 8 * a.nnz + 4 * (a.m + 1) + 4 * a.m),
     }
     assert lb.device_error() == 0
 

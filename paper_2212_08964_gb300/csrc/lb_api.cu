@@ -532,7 +532,7 @@ lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, 
     if (p->nnz == 0) return LB_OK;
     if (!col_idx || !g || !x || !dvalues) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, nullptr,
+    return from_cuda(launch_dvalues(p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, nullptr,
                                     dvalues, stream));
 }
 
@@ -542,7 +542,7 @@ lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float
     if (p->nnz == 0) return LB_OK;
     if (!g || !x_gathered || !dvalues) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, nullptr, g, nullptr,
+    return from_cuda(launch_dvalues(p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, nullptr, g, nullptr,
                                     x_gathered, dvalues, stream));
 }
 

@@ -178,7 +178,7 @@ cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m
 
 // dvalues over the forward partition: dv[k] = g[row(k)] * x[ci[k]], or, with xg non-null,
 // dv[k] = g[row(k)] * xg[k] from x gathers saved by the forward product (ci and x unused).
-cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
+cudaError_t launch_dvalues(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
                            const int *row_end, const int *ci, const float *g, const float *x, const float *xg,
                            float *dv, cudaStream_t stream);
 

@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                                                             const int *__restrict__ tile_nz,
                                                             const int *__restrict__ row_end,
                                                             const int *__restrict__ ci, const float *__restrict__ g,
-                                                            const float *__restrict__ x, const float *__restrict__ xg,
-                                                            float *__restrict__ dv, int *__restrict__ rowid) {
+                                                            const float *__restrict__ x, float *__restrict__ dv,
+                                                            int *__restrict__ rowid) {
     constexpr int T = THREADS * IPT;
     __shared__ int s_re[T];
     __shared__ int s_row[T];
@@ -246,8 +246,6 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                 const int row = r0 + s_row[j];
                 if (ROWID)
                     rowid[k] = row;
-                else if (xg != nullptr)
-                    __stcs(dv + k, __ldg(g + row) * __ldcs(xg + k));
                 else
                     dv[k] = __ldg(g + row) * __ldg(x + __ldg(ci + k));
             }
@@ -258,29 +256,144 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
 
 template <bool ROWID>
 static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, const int *tile_nz,
-                                    const int *row_end, const int *ci, const float *g, const float *x,
-                                    const float *xg, float *dv, int *rowid, cudaStream_t st) {
+                                    const int *row_end, const int *ci, const float *g, const float *x, float *dv,
+                                    int *rowid, cudaStream_t st) {
     if (G <= 0) return cudaSuccess;
     int grid = G;
     const int cap = current_sm_count() * 6;
     if (grid > cap) grid = cap;
     // The staged row ends must fit: a tile holds at most tile_items rows.
     if (tile_items <= 1024)
-        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, xg, dv, rowid);
+        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
     else if (tile_items <= 2048)
-        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, xg, dv, rowid);
+        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
     else if (tile_items <= 4096)
-        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, xg, dv, rowid);
+        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
+// dvalues[k] = g[row(k)] * xg[k] from the forward product's saved gathers: a streaming pass.
+// Per tile, every row end inside the tile adds 1 to a per-slot count in shared memory; the row
+// of a slot is then the inclusive prefix sum of the counts (each thread sums its IPT slots,
+// the block scans the thread totals), so no search is needed.  Slots are aligned so that
+// slot 0 of a tile sits on a 16-byte boundary of xg (the tile's first nonzero at slot `lead`),
+// and each thread moves its IPT consecutive values with vector loads and stores when they all
+// belong to the tile (and dv has xg's alignment).
+template <int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS) dvalues_saved_kernel(int G, int m, const int *__restrict__ tile_row,
+                                                                const int *__restrict__ tile_nz,
+                                                                const int *__restrict__ row_end,
+                                                                const float *__restrict__ g,
+                                                                const float *__restrict__ xg, float *__restrict__ dv) {
+    constexpr int T = THREADS * IPT;
+    constexpr int WARPS = THREADS / 32;
+    static_assert(IPT % 4 == 0, "slots move four at a time");
+    __shared__ __align__(16) int cnt[T];
+    __shared__ int wsum[WARPS];
+    for (int i = threadIdx.x; i < T; i += THREADS) cnt[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec_dv = ((reinterpret_cast<uintptr_t>(dv) - reinterpret_cast<uintptr_t>(xg)) & 15u) == 0;
+    const int xg_word = static_cast<int>((reinterpret_cast<uintptr_t>(xg) >> 2) & 3u);
+    for (int tile = blockIdx.x; tile < G; tile += gridDim.x) {
+        const int r0 = __ldg(tile_row + tile), r1 = __ldg(tile_row + tile + 1);
+        const int k0 = __ldg(tile_nz + tile), k1 = __ldg(tile_nz + tile + 1);
+        const int nr = r1 - r0, nk = k1 - k0;
+        const int lead = (xg_word + k0) & 3;  // xg + k0 - lead is 16-byte aligned
+        if (nr < 0 || nk < 0 || nk + lead > T) continue;  // malformed offsets (block-uniform)
+        for (int r = threadIdx.x; r < nr; r += THREADS) {
+            const int e = __ldg(row_end + r0 + r) - k0;  // first nonzero of the next row, tile-local
+            if (e >= 0 && e < nk) atomicAdd(&cnt[e + lead], 1);
+        }
+        __syncthreads();
+        const int s0 = threadIdx.x * IPT;
+        int c[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; q += 4) {
+            const int4 t = *reinterpret_cast<const int4 *>(cnt + s0 + q);
+            c[q] = t.x;
+            c[q + 1] = t.y;
+            c[q + 2] = t.z;
+            c[q + 3] = t.w;
+            *reinterpret_cast<int4 *>(cnt + s0 + q) = make_int4(0, 0, 0, 0);  // ready for the next tile
+        }
+#pragma unroll
+        for (int q = 1; q < IPT; ++q) c[q] += c[q - 1];
+        const int tot = c[IPT - 1];
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        int base = incl - tot;
+        for (int w = 0; w < warp; ++w) base += wsum[w];
+        const int j0 = s0 - lead;  // tile item of this thread's first slot
+        if (j0 + IPT > 0 && j0 < nk) {
+            const bool full = j0 >= 0 && j0 + IPT <= nk;
+            const float *src = xg + k0 + j0;
+            float *dst = dv + k0 + j0;
+            float xv[IPT];
+            if (full) {
+#pragma unroll
+                for (int q = 0; q < IPT; q += 4) {
+                    const float4 t = __ldcs(reinterpret_cast<const float4 *>(src + q));
+                    xv[q] = t.x;
+                    xv[q + 1] = t.y;
+                    xv[q + 2] = t.z;
+                    xv[q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) xv[q] = (j0 + q >= 0 && j0 + q < nk) ? __ldcs(src + q) : 0.f;
+            }
+            float o[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int row = r0 + base + c[q];
+                o[q] = (j0 + q >= 0 && j0 + q < nk && row < m) ? __ldg(g + row) * xv[q] : 0.f;
+            }
+            if (full && vec_dv) {
+#pragma unroll
+                for (int q = 0; q < IPT; q += 4)
+                    __stcs(reinterpret_cast<float4 *>(dst + q), make_float4(o[q], o[q + 1], o[q + 2], o[q + 3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (j0 + q >= 0 && j0 + q < nk) __stcs(dst + q, o[q]);
+            }
+        }
+        __syncthreads();  // wsum and the counts are reused by the next tile
+    }
+}
+
+cudaError_t launch_dvalues(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
                            const int *row_end, const int *ci, const float *g, const float *x, const float *xg,
                            float *dv, cudaStream_t stream) {
-    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, xg, dv, nullptr,
-                                   stream);
+    if (xg == nullptr)
+        return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, dv, nullptr,
+                                       stream);
+    if (num_tiles <= 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(xg) & 3u) != 0) return cudaErrorInvalidValue;  // float arrays
+    // A tile's slots: its items plus a lead of up to 3 must fit.
+    long long grid = static_cast<long long>(current_sm_count()) * 8;
+    if (tile_items + 3 <= 2048) {
+        if (grid > num_tiles) grid = num_tiles;
+        dvalues_saved_kernel<256, 8><<<static_cast<int>(grid), 256, 0, stream>>>(num_tiles, m, tile_row, tile_nz,
+                                                                                 row_end, g, xg, dv);
+    } else if (tile_items + 3 <= 4096) {
+        grid /= 2;
+        if (grid > num_tiles) grid = num_tiles;
+        dvalues_saved_kernel<512, 8><<<static_cast<int>(grid), 512, 0, stream>>>(num_tiles, m, tile_row, tile_nz,
+                                                                                 row_end, g, xg, dv);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -315,7 +428,7 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
         cudaSuccess)
         goto done;
     if ((e = launch_tile_rows<true>(num_tiles, tile_items, tile_row, tile_nz, ro + 1, nullptr, nullptr, nullptr,
-                                    nullptr, nullptr, rowid, st)) != cudaSuccess)
+                                    nullptr, rowid, st)) != cudaSuccess)
         goto done;
     {
         int bits = 0;
