@@ -48,8 +48,8 @@ namespace lb {
 
 // Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.  SV is
 // the size of the third staged array (values, or CSR positions for the transposed product);
-// NS is the number of shared-memory stages.
-template <int GW, int IPT, int SV, int NS>
+// NS is the number of shared-memory stages, NB the number of product buffers.
+template <int GW, int IPT, int SV, int NS, int NB>
 struct MergeShape {
     static_assert(IPT == 8 || IPT == 16, "items per thread: 8 or 16 (one byte or halfword of flags)");
     static constexpr int GT = GW * 32;   // gather threads
@@ -73,7 +73,8 @@ struct MergeShape {
     // position and carry-in.  Buffers start 128-byte aligned (accessed as float4).
     static constexpr size_t BUF = (static_cast<size_t>(P_FLOATS) * 4 + 3 * GT * 4 + 127) / 128 * 128;
     static_assert((P_FLOATS * 4) % 16 == 0, "slot values must keep 16-byte alignment");
-    static constexpr size_t SMEM = HDR + NSTAGE * static_cast<size_t>(STAGE) + BITS + 2 * BUF;
+    static constexpr int NBUF = NB;
+    static constexpr size_t SMEM = HDR + NSTAGE * static_cast<size_t>(STAGE) + BITS + NBUF * BUF;
     // Resident CTAs per SM from shared memory (228 KB per SM, 1 KB reserved per CTA), capped
     // by a register budget of 56 per thread.
     static constexpr int BY_SMEM = static_cast<int>((228 * 1024) / (SMEM + 1024));
@@ -169,6 +170,7 @@ struct MergeTraits {
     // leave more of the SM's unified L1/shared memory to the L1 and measure faster for it,
     // while the forward product measures faster with three.
     static constexpr int NS = (MODE == kTransposed) ? 2 : 3;
+    static constexpr int NB = 2;  // product buffers
     __device__ static const void *third(const MergeArgs &a) {
         return (MODE == kTransposed) ? static_cast<const void *>(a.perm) : a.val;
     }
@@ -541,11 +543,13 @@ __device__ __forceinline__ bool group_bar_any(bool pred) {
 }
 
 template <typename V, int GW, int IPT, int MODE>
-__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>::THREADS,
-                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>::MIN_BLOCKS)
+__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>::THREADS,
+                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>::MIN_BLOCKS)
     merge_spmv_kernel(const MergeArgs a) {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>;
     constexpr int NS = Sh::NSTAGE;
+    constexpr int NB = Sh::NBUF;
+    static_assert(NB >= 1 && NB <= 2, "one or two product buffers");
     static_assert(NS <= static_cast<int>(sizeof(Bars::full) / sizeof(uint64_t)), "one barrier set per stage");
     constexpr int GT = Sh::GT;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -594,9 +598,9 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
         // runs at its own pace.
         const int g = tid;
         for (int i = 0; i < n_my; ++i) {
-            const int s = i % NS, b = i & 1;
+            const int s = i % NS, b = i % NB;
             bool ok = mbar_wait_bounded(&bars->full[s], (i / NS) & 1, kWaitLimitNs);
-            if (ok && i >= 2) ok = mbar_wait_bounded(&bars->pfree[b], ((i - 2) >> 1) & 1, kWaitLimitNs);
+            if (ok && i >= NB) ok = mbar_wait_bounded(&bars->pfree[b], ((i - NB) / NB) & 1, kWaitLimitNs);
             if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
                 if (lane == 0) atomicExch(a.err, static_cast<int>(LB_ERR_TIMEOUT));
                 return;
@@ -640,8 +644,8 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
         static_assert(PER % 4 == 0, "aggregates are read four at a time");
         const int st = tid - GT;
         for (int i = 0; i < n_my; ++i) {
-            const int s = i % NS, b = i & 1;
-            bool ok = mbar_wait_bounded(&bars->pready[b], (i >> 1) & 1, kWaitLimitNs);
+            const int s = i % NS, b = i % NB;
+            bool ok = mbar_wait_bounded(&bars->pready[b], (i / NB) & 1, kWaitLimitNs);
             if (ok) ok = mbar_wait_bounded(&bars->full[s], (i / NS) & 1, kWaitLimitNs);
             const ProdBuf<GT> pb = buf(b);
             if (ok && st < 32) {
@@ -761,7 +765,7 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
 // device; also raises the kernel's dynamic shared-memory limit).
 template <typename V, int GW, int IPT, int MODE>
 int merge_blocks_per_sm() {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>;
     constexpr int kMaxDev = 64;
     static int cache[kMaxDev] = {0};
     static std::mutex mu;
@@ -776,14 +780,26 @@ int merge_blocks_per_sm() {
             return 0;
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Sh::THREADS, Sh::SMEM) != cudaSuccess) return 0;
-        cache[dev] = nb > 0 ? nb : 1;
+        nb = nb > 0 ? nb : 1;
+        // Ask for no more shared memory than the resident CTAs use: the rest of the SM's
+        // unified L1/shared memory stays L1, which holds the random gathers in flight (their
+        // rate falls steeply as the L1 share shrinks).
+        int max_smem = 0;
+        if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            max_smem <= 0)
+            return 0;
+        const long long need = static_cast<long long>(nb) * (Sh::SMEM + 1024);
+        int pct = static_cast<int>((need * 100 + max_smem - 1) / max_smem);
+        if (pct > 100) pct = 100;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess) return 0;
+        cache[dev] = nb;
     }
     return cache[dev];
 }
 
 template <typename V, int GW, int IPT, int MODE>
 cudaError_t launch_merge_cfg(const MergeArgs &a, cudaStream_t st, cudaEvent_t eb, cudaEvent_t ea) {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>;
     const int per_sm = merge_blocks_per_sm<V, GW, IPT, MODE>();
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const long long wave = static_cast<long long>(per_sm) * current_sm_count();
