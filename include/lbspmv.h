@@ -247,6 +247,38 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat,
 void lb_batched_plan_destroy(lb_batched_plan *p);
 
 /*
+ * Autotuner timing core.  The dissertation chooses a schedule by a fixed size rule (Ch.4 Sec.
+ * "Improved Performance Response"); lb_tune measures instead.  Every candidate schedule and
+ * launch shape this build implements (merge-path at each shape, thread-mapped, warp-mapped,
+ * group-mapped with 4, 8 and 16 lanes, block-mapped with 128 and 256 threads) builds a plan
+ * and runs y = A x `reps` times on `stream`, timed by CUDA events after one untimed call.
+ * Results (schedule, resolved tuning, mean milliseconds) are written sorted fastest first,
+ * at most `capacity` of them; *count receives how many.  y (m floats, device) is scratch
+ * and is left holding A x.  Creates and destroys plans (allocates) and synchronizes the
+ * stream.  lb_tune_candidates() is the number of candidates.
+ */
+typedef struct {
+    lb_schedule schedule;
+    lb_tuning tuning;
+    float ms;
+} lb_tune_result;
+
+int lb_tune_candidates(void);
+
+lb_status lb_tune(int m, int n, int nnz, const int *row_offsets, const int *col_idx, const void *values,
+                  lb_dtype vdt, const float *x, float *y, int reps, lb_tune_result *results, int capacity,
+                  int *count, cudaStream_t stream);
+
+/*
+ * The same for a batch run as one block-diagonal merge path (arguments as for
+ * lb_batched_plan_create and lb_spmv_batched): every merge-path launch shape, timed.
+ */
+lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *h_nnz,
+                          const int *row_offsets_concat, const int *col_idx_concat, const void *values_concat,
+                          lb_dtype vdt, const float *x_concat, float *y_concat, int reps,
+                          lb_tune_result *results, int capacity, int *count_out, cudaStream_t stream);
+
+/*
  * Check a CSR matrix on the device and write a bit mask to the device int *d_status
  * (0 = valid): 1 row_offsets[0] != 0; 2 row_offsets decreasing somewhere; 4
  * row_offsets[m] != nnz; 8 a column index outside [0, n); 16 (only with check_sorted)

@@ -1,0 +1,172 @@
+"""Autotuner: schedule and launch shape per matrix-shape class, chosen by measurement.
+
+The dissertation chooses between its schedules with a fixed rule of matrix size (Ch.4 Sec.
+"Improved Performance Response": merge-path unless rows or columns are below 500 and the
+nonzeros below 10000).  The rule cannot see row-length skew or the hardware it runs on.  This
+module keeps a table from *shape classes* to the schedule and launch shape that measured
+fastest for that class (``lb_tune`` in the library times every candidate on the device); a
+matrix of a class already in the table gets the recorded winner, any other matrix gets the
+dissertation's rule (``"auto"``).
+
+A shape class is computed on the host from the row lengths:
+
+* ``size``: log2 of the work items m + nnz (rounded down);
+* ``mean``: log2 of the mean row length nnz / m, in half-octave steps;
+* ``skew``: the longest row over the mean row length, bucketed to 1, 4, 32, 256 and above;
+* ``dtype``: the value type.
+
+Batches are classed by the batch count and total work (log2), and the dominant member class.
+The table is a plain dict that round-trips through JSON (``save`` / ``load``).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+
+import numpy as np
+
+from . import lbspmv
+
+__all__ = ["shape_class", "batch_class", "Table", "tune", "tune_batched", "choose", "plan_for"]
+
+_SKEW_EDGES = (1.5, 4.0, 32.0, 256.0)
+_DTYPE_NAMES = {0: "f32", 1: "bf16", 2: "f16"}
+
+
+def _row_lengths(row_offsets) -> np.ndarray:
+    ro = np.asarray(row_offsets, dtype=np.int64)
+    return np.diff(ro)
+
+
+def shape_class(row_offsets, dtype: str = "f32") -> str:
+    """Class key of a CSR matrix from its (host) row offsets."""
+    lengths = _row_lengths(row_offsets)
+    m = int(lengths.shape[0])
+    nnz = int(lengths.sum()) if m else 0
+    size = int(math.floor(math.log2(m + nnz))) if m + nnz > 0 else 0
+    mean = nnz / m if m else 0.0
+    mean_b = int(math.floor(2.0 * math.log2(mean))) if mean > 0 else -99
+    skew = (float(lengths.max()) / mean) if mean > 0 else 0.0
+    skew_b = sum(1 for e in _SKEW_EDGES if skew >= e)
+    return f"size{size}-mean{mean_b}-skew{skew_b}-{dtype}"
+
+
+def batch_class(ms, nnzs, row_offsets_concat, dtype: str = "f32") -> str:
+    """Class key of a batch: count and total work (log2), and the class of the member holding
+    the most work."""
+    ms = np.asarray(ms, np.int64)
+    nnzs = np.asarray(nnzs, np.int64)
+    count = int(ms.shape[0])
+    work = ms + nnzs
+    total = int(work.sum())
+    big = int(np.argmax(work)) if count else 0
+    start = int((ms[:big] + 1).sum())
+    member = shape_class(np.asarray(row_offsets_concat)[start: start + int(ms[big]) + 1], dtype) if count else "none"
+    c = int(math.floor(math.log2(count))) if count else 0
+    t = int(math.floor(math.log2(total))) if total else 0
+    return f"batch{c}-work{t}-[{member}]"
+
+
+class Table:
+    """Shape class -> winning configuration, with the measured candidates."""
+
+    def __init__(self, entries: dict | None = None):
+        self.entries: dict[str, dict] = dict(entries or {})
+
+    def record(self, key: str, results: list[dict]):
+        if not results:
+            raise ValueError("no tuning results to record")
+        best = min(results, key=lambda r: r["ms"])
+        self.entries[key] = {"best": {k: best[k] for k in ("schedule", "threads", "items_per_thread", "group_size")},
+                             "ms": best["ms"], "candidates": results}
+
+    def lookup(self, key: str) -> dict | None:
+        e = self.entries.get(key)
+        return dict(e["best"]) if e else None
+
+    def save(self, path: str):
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(self.entries, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+    @classmethod
+    def load(cls, path: str) -> "Table":
+        with open(path) as f:
+            return cls(json.load(f))
+
+
+def _results(buf, count: int) -> list[dict]:
+    names = {v: k for k, v in lbspmv.SCHEDULES.items()}
+    out = []
+    for i in range(count):
+        r = buf[i]
+        out.append({"schedule": names[r.schedule], "threads": r.tuning.threads,
+                    "items_per_thread": r.tuning.items_per_thread, "group_size": r.tuning.group_size,
+                    "ms": float(r.ms)})
+    return out
+
+
+def tune(row_offsets, col_idx, values, x, n: int | None = None, reps: int = 20, table: Table | None = None,
+         stream=None) -> list[dict]:
+    """Time every schedule and launch shape on this matrix (device tensors); returns the
+    candidates fastest first and, with ``table``, records the winner for the matrix's class."""
+    import torch
+
+    lib = lbspmv.ensure_loaded()
+    m = row_offsets.numel() - 1
+    nnz = col_idx.numel()
+    n = x.numel() if n is None else int(n)
+    y = torch.empty(m, dtype=torch.float32, device=x.device)
+    cap = int(lib.lb_tune_candidates())
+    buf = (lbspmv.TuneResult * cap)()
+    cnt = ctypes.c_int()
+    lbspmv._check(lib.lb_tune(m, n, nnz, row_offsets.data_ptr(), col_idx.data_ptr(), values.data_ptr(),
+                              lbspmv._vdt(values), x.data_ptr(), y.data_ptr(), int(reps), buf, cap, ctypes.byref(cnt),
+                              lbspmv._stream(stream)), "lb_tune")
+    res = _results(buf, cnt.value)
+    if table is not None:
+        dt = _DTYPE_NAMES[lbspmv._vdt(values)]
+        table.record(shape_class(row_offsets.cpu().numpy(), dt), res)
+    return res
+
+
+def tune_batched(ms, ns, nnzs, row_offsets_concat, col_idx_concat, values_concat, x_concat, reps: int = 10,
+                 table: Table | None = None, stream=None) -> list[dict]:
+    """Time every merge-path launch shape on this batch; with ``table``, record the winner."""
+    import torch
+
+    lib = lbspmv.ensure_loaded()
+    ms32 = np.ascontiguousarray(ms, np.int32)
+    ns32 = np.ascontiguousarray(ns, np.int32)
+    nz32 = np.ascontiguousarray(nnzs, np.int32)
+    y = torch.empty(int(ms32.astype(np.int64).sum()), dtype=torch.float32, device=x_concat.device)
+    cap = int(lib.lb_tune_candidates())
+    buf = (lbspmv.TuneResult * cap)()
+    cnt = ctypes.c_int()
+    lbspmv._check(lib.lb_tune_batched(int(ms32.shape[0]), ms32.ctypes.data, ns32.ctypes.data, nz32.ctypes.data,
+                                      row_offsets_concat.data_ptr(), col_idx_concat.data_ptr(),
+                                      values_concat.data_ptr(), lbspmv._vdt(values_concat), x_concat.data_ptr(),
+                                      y.data_ptr(), int(reps), buf, cap, ctypes.byref(cnt), lbspmv._stream(stream)),
+                  "lb_tune_batched")
+    res = _results(buf, cnt.value)
+    if table is not None:
+        dt = _DTYPE_NAMES[lbspmv._vdt(values_concat)]
+        table.record(batch_class(ms, nnzs, row_offsets_concat.cpu().numpy(), dt), res)
+    return res
+
+
+def choose(row_offsets, table: Table | None, dtype: str = "f32") -> dict:
+    """The configuration for a matrix: the table's winner for its class, else the
+    dissertation's size rule (schedule "auto")."""
+    best = table.lookup(shape_class(row_offsets, dtype)) if table is not None else None
+    return best if best is not None else {"schedule": "auto", "threads": 0, "items_per_thread": 0, "group_size": 0}
+
+
+def plan_for(row_offsets, n: int, table: Table | None, dtype: str = "f32", stream=None) -> "lbspmv.Plan":
+    """A Plan built with ``choose``'s configuration (row_offsets: int32 device tensor)."""
+    cfg = choose(row_offsets.cpu().numpy(), table, dtype)
+    return lbspmv.Plan(row_offsets, n, schedule=cfg["schedule"], threads=cfg["threads"],
+                       items_per_thread=cfg["items_per_thread"], group_size=cfg["group_size"], stream=stream)

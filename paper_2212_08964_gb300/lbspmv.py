@@ -75,6 +75,12 @@ class _Tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("items_per_thread", ctypes.c_int), ("group_size", ctypes.c_int)]
 
 
+class TuneResult(ctypes.Structure):
+    """lb_tune_result: a candidate's schedule, resolved launch shape and mean milliseconds."""
+
+    _fields_ = [("schedule", ctypes.c_int), ("tuning", _Tuning), ("ms", ctypes.c_float)]
+
+
 _lib = None
 _lock = threading.Lock()
 _P = ctypes.c_void_p
@@ -106,11 +112,15 @@ def _declare(lib):
         "lb_validate_csr": [_I, _I, _I, _P, _P, _I, _P, _P],
         "lb_device_error": [ctypes.POINTER(_I), _I],
         "lb_set_profile_events": [_P, _P],
+        "lb_tune": [_I, _I, _I, _P, _P, _P, _I, _P, _P, _I, _P, _I, ctypes.POINTER(_I), _P],
+        "lb_tune_batched": [_I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _I, _P, _I, ctypes.POINTER(_I), _P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = _I
+    lib.lb_tune_candidates.argtypes = []
+    lib.lb_tune_candidates.restype = _I
     lib.lb_num_tiles.argtypes = [_I, _I, _I]
     lib.lb_num_tiles.restype = _I
     lib.lb_plan_destroy.argtypes = [_P]
