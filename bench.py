@@ -7,8 +7,9 @@ rows up to 500k), with the plan (merge-path partition, CSC view) built once per 
 
   forward   y  = A x      lb_spmv_planned_save: persistent merge-path SpMV + carry fixup, also
                           saving x[col] of every nonzero for the values gradient
-  backward  dx = A^T g    lb_spmv_t: value buckets + merge-path over the CSC view + fixup
-            dv = g . x    lb_spmv_dvalues_gathered: per-nonzero map over the forward partition
+  backward  dv = g . x    lb_spmv_backward: one CSR-order pass over the forward partition forms
+            dx = A^T g    dvalues and the scaled values v * g[row] in L2-sized buckets of CSC
+                          order; a merge-path gather-sum over the CSC view + fixup forms dx
 
 The partition alone and the one-shot lb_spmv (partition + SpMV + fixup every call) are timed
 separately and reported under config.components_us.
@@ -329,12 +330,11 @@ def run_ours(args):
 
     def step(vals, xx, gg):
         # The training step of y = A x under autograd: forward (saving x[col] per nonzero for
-        # the values gradient), then dx = A^T g and dvalues = g[row] * x[col].
+        # the values gradient), then dx = A^T g and dvalues = g[row] * x[col] together.
         plan.spmv(ci, vals, xx, out=y, save_gathered=xg)
-        plan.spmv_t(vals, gg, out=dx)
-        plan.dvalues_gathered(gg, xg, out=dv)
+        plan.backward(vals, gg, xg, dx=dx, dvalues=dv)
 
-    launches_per_step = 2 + 3 + 1
+    launches_per_step = 2 + 3
     fwd_b, bwd_t_b, dv_b = step_bytes(a.m, a.n, a.nnz)
     total_b = fwd_b + bwd_t_b + dv_b
 
@@ -356,12 +356,10 @@ def run_ours(args):
             # on the launching stream for the merge-path kernels).
             lb.set_profile_events(evf_b[i], evf_a[i])
             plan.spmv(ci, v, xd, out=y, save_gathered=xg)
+            evd_b[i].record()  # the CSR-order backward pass runs first in lb_spmv_backward
             lb.set_profile_events(evt_b[i], evt_a[i])
-            plan.spmv_t(v, gd, out=dx)
+            plan.backward(v, gd, xg, dx=dx, dvalues=dv)
             lb.set_profile_events(None, None)
-            evd_b[i].record()
-            plan.dvalues_gathered(gd, xg, out=dv)
-            evd_a[i].record()
         t1.record()
         torch.cuda.synchronize()
     lb.set_profile_events(None, None)
@@ -370,10 +368,16 @@ def run_ours(args):
     ms = t0.elapsed_time(t1) / K
     ms_max = max_over_ranks(ms, world)
     mean_ms = lambda b, e: float(np.mean([x.elapsed_time(y_) for x, y_ in zip(b, e)]))  # noqa: E731
+    # Backward bytes: the CSR-order pass reads values, saved gathers and row offsets and writes
+    # dvalues and the scaled values; the gather-sum streams CSC offsets and positions, gathers
+    # the scaled values and writes dx.  Both counted at their minimum (every array once).
+    vb = 4
+    csr_b = a.nnz * (vb + 4 + 4 + 4) + 4 * (a.m + 1) + 4 * a.m
+    gs_b = a.nnz * (4 + 4) + 4 * (a.n + 1) + 4 * a.n
     kern = {
         "merge_spmv_kernel<plain> (y = A x, saving x[col])": (mean_ms(evf_b, evf_a), fwd_b + 4 * a.nnz),
-        "merge_spmv_kernel<transposed> (dx = A^T g)": (mean_ms(evt_b, evt_a), bwd_t_b),
-        "dvalues_saved_kernel (dvalues from the saved gathers)": (mean_ms(evd_b, evd_a), 8 * a.nnz + 4 * (a.m + 1) + 4 * a.m),
+        "csr_backward_kernel (dvalues, v*g[row] into CSC buckets)": (mean_ms(evd_b, evt_b), csr_b),
+        "merge_spmv_kernel<gather-sum> (dx = A^T g)": (mean_ms(evt_b, evt_a), gs_b),
     }
     assert lb.device_error() == 0
 
@@ -396,6 +400,7 @@ def run_ours(args):
         "forward_oneshot_lb_spmv_us": 1e3 * _time(torch, lambda: lb.spmv(ro, ci, v, xd, out=y), 20),
         "forward_planned_us": 1e3 * _time(torch, lambda: plan.spmv(ci, v, xd, out=y), 20),
         "dvalues_gathering_x_us": 1e3 * _time(torch, lambda: plan.dvalues(ci, gd, xd, out=dv), 20),
+        "spmv_t_us": 1e3 * _time(torch, lambda: plan.spmv_t(v, gd, out=dx), 20),
     }
 
     result = {
@@ -407,7 +412,7 @@ def run_ours(args):
             "schedule": info["schedule"], "threads": info["threads"], "items_per_thread": info["items_per_thread"],
             "num_tiles": info["num_tiles"], "parallelism": f"replicas x{world}",
             "step": "plan built once per structure (partition, CSC view); per step: forward saving x[col], "
-                    "dx = A^T g, dvalues from the saved gathers",
+                    "then dvalues and dx = A^T g (CSR-order pass + merge-path gather-sum over the CSC view)",
             "l2": f"no flush: each step streams {total_b / 1e9:.2f} GB of inputs, above the 129 MB L2",
             "bytes_per_step": {"forward": fwd_b, "backward_dx": bwd_t_b, "backward_dvalues": dv_b},
             "components_us": comp,

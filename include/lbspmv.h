@@ -179,9 +179,15 @@ lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t s
 lb_status lb_plan_transpose(const lb_plan *p, int *col_offsets, int *row_idx, int *perm);
 
 /*
- * dx = A^T g (backward of y = A x with respect to x): merge-path SpMV over the CSC view,
- * tiles = columns, atoms = CSC entries, values read in CSR order through perm.  Requires
- * lb_plan_build_transpose.  g: m floats, dx: n floats (overwritten).
+ * dx = A^T g (backward of y = A x with respect to x) over the CSC view, in two passes.  First,
+ * one streaming pass over the nonzeros in CSR order forms the scaled values v[k] * g[row(k)]
+ * (row(k) from the forward partition) and writes them into L2-sized buckets of CSC order
+ * (plan memory, 4 bytes per nonzero).  Then a merge-path pass over the CSC view (tiles =
+ * columns, atoms = CSC entries) sums, per column, the scaled values gathered from the bucket
+ * being worked on, and the fixup adds the carries.  The summation order (CSC order within a
+ * column) and the product rounding are fixed, so dx is deterministic.  Requires
+ * lb_plan_build_transpose.  g: m floats, dx: n floats (overwritten).  Not safe to run
+ * concurrently with another lb_spmv_t / lb_spmv_backward on the same plan (shared scratch).
  */
 lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
                     cudaStream_t stream);
@@ -211,6 +217,16 @@ lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void 
  */
 lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
                                    cudaStream_t stream);
+
+/*
+ * Both gradients of y = A x in one go: dvalues[k] = g[row(k)] * x_gathered[k] (x_gathered from
+ * lb_spmv_planned_save) is formed in the same CSR-order pass that prepares the scaled values
+ * for dx = A^T g (see lb_spmv_t), so the backward is two passes over the nonzeros instead of
+ * three.  Results equal lb_spmv_t's dx and lb_spmv_dvalues_gathered's dvalues bit for bit.
+ * Requires lb_plan_build_transpose; dx (n floats) and dvalues (nnz floats) are overwritten.
+ */
+lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
+                           const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream);
 
 void lb_plan_destroy(lb_plan *p);
 
@@ -297,8 +313,8 @@ lb_status lb_device_error(int *status, int clear);
 
 /*
  * Profiling aid: while set (non-NULL), every merge-path SpMV call (lb_spmv, lb_spmv_planned,
- * lb_spmv_planned_save, lb_spmv_t, lb_spmv_batched) records `before` right before and `after`
- * right after its main kernel on the call's stream.  Process-wide, not thread-safe; pass
+ * lb_spmv_planned_save, lb_spmv_t, lb_spmv_backward, lb_spmv_batched) records `before` right
+ * before and `after` right after its merge-path kernel on the call's stream.  Process-wide, not thread-safe; pass
  * NULLs to stop.
  */
 lb_status lb_set_profile_events(cudaEvent_t before, cudaEvent_t after);

@@ -148,9 +148,9 @@ struct lb_plan {
     int *co = nullptr, *ri = nullptr, *perm = nullptr;
     int *t_tile_row = nullptr, *t_tile_nz = nullptr, *t_carry_row = nullptr;
     float *t_carry_val = nullptr;
-    int bucket_shift = 0;  // 0: values are gathered straight through perm (one L2-sized bucket)
+    int bucket_shift = 0;  // 0: one L2-sized bucket (CSR order, gathered through perm)
     int *bucket_pos = nullptr, *bucket_perm = nullptr;
-    void *bucket_vals = nullptr;  // per-call CSR values in bucket order (4 bytes per entry)
+    float *pv = nullptr;  // per call: values[k] * g[row(k)] in bucket order (nnz floats)
 };
 
 struct lb_batched_plan {
@@ -174,8 +174,8 @@ static void release_transpose(lb_plan *p) {
     }
     if (p->t_carry_val) cudaFree(p->t_carry_val);
     p->t_carry_val = nullptr;
-    if (p->bucket_vals) cudaFree(p->bucket_vals);
-    p->bucket_vals = nullptr;
+    if (p->pv) cudaFree(p->pv);
+    p->pv = nullptr;
     p->bucket_shift = 0;
 }
 
@@ -451,12 +451,12 @@ lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t s
     TransposeOut out{p->co, p->ri, p->perm};
     e = build_transpose(p->m, n, nnz, p->ro, col_idx, p->G, p->tile_items, p->tile_row, p->tile_nz, out, stream);
     if (e == cudaSuccess && nnz > 0) {
+        e = dmalloc(&p->pv, static_cast<size_t>(nnz));
         const int shift = value_bucket_shift(nnz);
-        if (((static_cast<long long>(nnz) - 1) >> shift) > 0) {  // more than one bucket
+        if (e == cudaSuccess && ((static_cast<long long>(nnz) - 1) >> shift) > 0) {  // more than one bucket
             p->bucket_shift = shift;
             if ((e = dmalloc(&p->bucket_pos, static_cast<size_t>(nnz))) == cudaSuccess &&
-                (e = dmalloc(&p->bucket_perm, static_cast<size_t>(nnz))) == cudaSuccess &&
-                (e = cudaMalloc(&p->bucket_vals, static_cast<size_t>(nnz) * 4)) == cudaSuccess)
+                (e = dmalloc(&p->bucket_perm, static_cast<size_t>(nnz))) == cudaSuccess)
                 e = build_value_buckets(nnz, shift, p->perm, p->bucket_pos, p->bucket_perm, stream);
         }
     }
@@ -489,15 +489,16 @@ lb_status lb_plan_transpose(const lb_plan *p, int *col_offsets, int *row_idx, in
     return from_cuda(e);
 }
 
-lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
-                    cudaStream_t stream) {
-    if (!p || !p->has_t || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
-    if (p->n == 0) return LB_OK;
-    if (!dx || (p->nnz > 0 && (!values || !g))) return LB_ERR_INVALID_ARG;
-    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream));
+// dx = A^T g in two passes over the plan's CSC view: the scaled values v[k] * g[row(k)] in CSR
+// order into L2-sized buckets of CSC order (with dvalues alongside when asked), then the
+// merge-path gather-sum over the columns.
+static lb_status transposed_product(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
+                                    const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream) {
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
+    cudaError_t e = launch_csr_backward(vdt, p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, g, values,
+                                        p->bucket_pos, p->pv, x_gathered, dvalues, stream);
+    if (e != cudaSuccess) return from_cuda(e);
     MergeArgs a{};
     a.num_tiles = p->Gt;
     a.num_rows = p->n;
@@ -505,25 +506,35 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
     a.tile_row = p->t_tile_row;
     a.tile_nz = p->t_tile_nz;
     a.row_end = p->co + 1;
-    a.idx = p->ri;
-    a.val = values;
-    a.perm = p->perm;
-    if (p->bucket_shift > 0) {
-        // Values into bucket order first; the transposed kernel then gathers within L2.
-        const int eb = vdt == LB_F32 ? 4 : 2;
-        cudaError_t e = launch_bucket_values(p->nnz, eb, values, p->bucket_pos, p->bucket_vals, stream);
-        if (e != cudaSuccess) return from_cuda(e);
-        a.val = p->bucket_vals;
-        a.perm = p->bucket_perm;
-    }
-    a.x = g;
+    a.idx = p->bucket_shift > 0 ? p->bucket_perm : p->perm;
+    a.x = p->pv;
     a.y = dx;
     a.carry_row = p->t_carry_row;
     a.carry_val = p->t_carry_val;
     a.err = err;
     const int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
     const int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
-    return from_cuda(launch_merge_spmv(vdt, kTransposed, threads, ipt, a, stream, g_ev_before, g_ev_after));
+    return from_cuda(launch_merge_spmv(LB_F32, kGatherSum, threads, ipt, a, stream, g_ev_before, g_ev_after));
+}
+
+lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
+                    cudaStream_t stream) {
+    if (!p || !p->has_t || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
+    if (p->n == 0) return LB_OK;
+    if (!dx || (p->nnz > 0 && (!values || !g))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream));
+    return transposed_product(p, values, vdt, g, nullptr, dx, nullptr, stream);
+}
+
+lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
+                           const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream) {
+    if (!p || !p->has_t || !dtype_ok(vdt) || !dx || !dvalues) return LB_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!values || !g || !x_gathered)) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->n == 0) return LB_OK;
+    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream));
+    return transposed_product(p, values, vdt, g, x_gathered, dx, dvalues, stream);
 }
 
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
@@ -728,6 +739,7 @@ namespace lb {
 
 cudaError_t launch_merge_spmv(lb_dtype vdt, int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t stream,
                               cudaEvent_t ev_before, cudaEvent_t ev_after) {
+    if (mode == kGatherSum) return launch_merge_f32(mode, threads, ipt, a, stream, ev_before, ev_after);
     switch (vdt) {
         case LB_F32:
             return launch_merge_f32(mode, threads, ipt, a, stream, ev_before, ev_after);

@@ -137,8 +137,7 @@ struct MergeArgs {
     const int *tile_nz;   // [G+1] atoms consumed before each tile boundary
     const int *row_end;   // row_end[r] = offset one past the last atom of row r (offsets + 1)
     const int *idx;       // gather index per atom (column index; CSC row index when transposed)
-    const void *val;      // values: per atom, or per CSR nonzero when transposed
-    const int *perm;      // transposed only: CSR nonzero index of each atom
+    const void *val;      // values, per atom (unused by the gather-sum product)
     const float *x;       // gathered dense vector
     float *y;             // output, one entry per row
     int *carry_row;       // [G] row left open at the end of each tile
@@ -150,7 +149,10 @@ struct MergeArgs {
     int *err;                 // device error word
 };
 
-enum MergeMode { kPlain = 0, kBatched = 1, kTransposed = 2 };
+// kPlain: y[r] = sum of val[k] * x[idx[k]] over row r.  kBatched: the same over a batch, with
+// per-matrix column bases.  kGatherSum: y[r] = sum of x[idx[k]] (no values; the transposed
+// product gathers its precomputed scaled values this way).
+enum MergeMode { kPlain = 0, kBatched = 1, kGatherSum = 2 };
 
 // Launch the persistent merge-path kernel followed by the fixup kernel.  `grid` <= 0 picks
 // one wave of resident CTAs.  `ev_before` / `ev_after` (may be null) are recorded around the
@@ -192,16 +194,19 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
                             int tile_items, const int *tile_row, const int *tile_nz, TransposeOut out,
                             cudaStream_t stream);
 
-// L2-sized buckets for bringing CSR-ordered values into CSC order (see lb_transpose.cu).
+// L2-sized buckets for bringing CSR-ordered data into CSC order (see lb_transpose.cu).
 // log2 of the bucket size in CSC entries; one bucket means no bucketing is needed.
 int value_bucket_shift(long long nnz);
 // bucket_pos[k] (position of CSR entry k in bucket order) and bucket_perm[p] (position in
-// bucket order of the value CSC entry p needs), from perm.
+// bucket order of the entry CSC entry p needs), from perm.
 cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket_pos, int *bucket_perm,
                                 cudaStream_t stream);
-// tmp[bucket_pos[k]] = values[k] for every k (element size 2 or 4 bytes).
-cudaError_t launch_bucket_values(int nnz, int elem_bytes, const void *values, const int *bucket_pos, void *tmp,
-                                 cudaStream_t stream);
+// One streaming pass over the nonzeros in CSR order (forward partition): the scaled values
+// pv[pos(k)] = values[k] * g[row(k)] with pos = bucket_pos (identity when null), and, when xg
+// and dv are given, dv[k] = g[row(k)] * xg[k].
+cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+                                const int *tile_nz, const int *row_end, const float *g, const void *values,
+                                const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream);
 
 // Batched-plan helpers.
 cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *row_base, const int *nz_base,

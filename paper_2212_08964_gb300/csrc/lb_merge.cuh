@@ -62,8 +62,8 @@ struct MergeShape {
     static constexpr int GPS = GT / ST;           // gather threads per scan thread
     static constexpr int THREADS = GT + ST + 32;  // + one producer warp
     static constexpr int NSTAGE = NS;
-    // One stage: row ends (4 B per row), indices (4 B per atom), values or CSR positions
-    // (SV B per atom), each padded to 16 B at both ends.  rows + atoms <= T.
+    // One stage: row ends (4 B per row), indices (4 B per atom), values (SV B per atom, none
+    // for the gather-sum product), each padded to 16 B at both ends.  rows + atoms <= T.
     static constexpr int STAGE = ((4 + SV) * T + 128 + 127) / 128 * 128;
     static constexpr int P_FLOATS = T + (T / 32) * 4;  // slot values with 4 floats of padding per 32
     static constexpr int HDR = 512;                    // mbarriers + stage headers
@@ -164,16 +164,12 @@ __device__ __forceinline__ Seg make_seg(const void *base, long long e_lo, long l
 
 template <typename V, int MODE>
 struct MergeTraits {
-    static constexpr uint32_t SV = (MODE == kTransposed) ? 4u : static_cast<uint32_t>(sizeof(V));
-    // Stages: the transposed product keeps twice as many gathers in flight per thread (the
-    // value through its CSR position as well as g), and those need L1 capacity; two stages
-    // leave more of the SM's unified L1/shared memory to the L1 and measure faster for it,
-    // while the forward product measures faster with three.
-    static constexpr int NS = (MODE == kTransposed) ? 2 : 3;
-    static constexpr int NB = 2;  // product buffers
-    __device__ static const void *third(const MergeArgs &a) {
-        return (MODE == kTransposed) ? static_cast<const void *>(a.perm) : a.val;
-    }
+    // Bytes per atom of the staged values; the gather-sum product stages none (its atoms are
+    // the gathered values themselves).
+    static constexpr uint32_t SV = (MODE == kGatherSum) ? 0u : static_cast<uint32_t>(sizeof(V));
+    static constexpr int NSLICE = SV > 0 ? 3 : 2;  // staged arrays: row ends, indices[, values]
+    static constexpr int NS = 3;                   // stages
+    static constexpr int NB = 2;                   // product buffers
 };
 
 // A tile from a valid partition has rows + atoms <= TILE_ITEMS; anything else means the
@@ -231,13 +227,15 @@ __device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, 
         return;
     }
     constexpr uint32_t SV = MergeTraits<V, MODE>::SV;
+    constexpr int NSL = MergeTraits<V, MODE>::NSLICE;
+    constexpr unsigned kSliceMask = (1u << NSL) - 1u;
     if (!edge_tile(a, b.r0, b.r1, b.k0, b.k1)) {
-        // Interior tile: every slice's aligned superset lies inside its array.  Lanes 0, 1, 2
-        // each place one slice (row ends, indices, values).
-        if (lane < 3) {
+        // Interior tile: every slice's aligned superset lies inside its array.  Lanes 0, 1 (and
+        // 2) each place one slice (row ends, indices, values).
+        if (lane < NSL) {
             const uintptr_t base = lane == 0 ? reinterpret_cast<uintptr_t>(a.row_end)
                                              : (lane == 1 ? reinterpret_cast<uintptr_t>(a.idx)
-                                                          : reinterpret_cast<uintptr_t>(MergeTraits<V, MODE>::third(a)));
+                                                          : reinterpret_cast<uintptr_t>(a.val));
             const uint32_t sz = lane == 2 ? SV : 4u;
             const uint32_t e_lo = static_cast<uint32_t>(lane == 0 ? b.r0 : b.k0);
             const uint32_t e_hi = static_cast<uint32_t>(lane == 0 ? b.r1 : b.k1);
@@ -245,13 +243,13 @@ __device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, 
             const uintptr_t hi = base + static_cast<uintptr_t>(e_hi) * sz;
             const uintptr_t a0 = lo & ~static_cast<uintptr_t>(15);
             const uint32_t bytes = static_cast<uint32_t>(((hi + 15) & ~static_cast<uintptr_t>(15)) - a0);
-            const uint32_t b1 = __shfl_up_sync(0x7u, bytes, 1);
-            const uint32_t b2 = __shfl_up_sync(0x7u, bytes, 2);
+            const uint32_t b1 = __shfl_up_sync(kSliceMask, bytes, 1);
+            const uint32_t b2 = NSL > 2 ? __shfl_up_sync(kSliceMask, bytes, 2) : 0u;
             const uint32_t off = (lane >= 1 ? b1 : 0u) + (lane >= 2 ? b2 : 0u);
             const uint32_t first = off + static_cast<uint32_t>(lo & 15);
-            const uint32_t total = __shfl_sync(0x7u, off + bytes, 2);
-            const uint32_t f1 = __shfl_sync(0x7u, first, 1);
-            const uint32_t f2 = __shfl_sync(0x7u, first, 2);
+            const uint32_t total = __shfl_sync(kSliceMask, off + bytes, NSL - 1);
+            const uint32_t f1 = __shfl_sync(kSliceMask, first, 1);
+            const uint32_t f2 = NSL > 2 ? __shfl_sync(kSliceMask, first, 2) : 0u;
             if (lane == 0) {
                 hdr->r0 = b.r0;
                 hdr->r1 = b.r1;
@@ -265,7 +263,7 @@ __device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, 
                 hdr->ok = 1;
                 mbar_arrive_expect_tx(bar, total);
             }
-            __syncwarp(0x7u);  // the transaction count is armed before any copy lands
+            __syncwarp(kSliceMask);  // the transaction count is armed before any copy lands
             if (bytes) bulk_g2s(stage + off, reinterpret_cast<const void *>(a0), bytes, bar, pol);
         }
         return;
@@ -275,8 +273,17 @@ __device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, 
     Seg t[3];
     t[0] = make_seg(a.row_end, b.r0, b.r1, a.num_rows, 4, 0);
     t[1] = make_seg(a.idx, b.k0, b.k1, a.num_atoms, 4, t[0].next);
-    t[2] = make_seg(MergeTraits<V, MODE>::third(a), b.k0, b.k1, a.num_atoms, SV, t[1].next);
-    for (int q = lane; q < 48; q += 32) {
+    if (NSL > 2) {
+        t[2] = make_seg(a.val, b.k0, b.k1, a.num_atoms, SV, t[1].next);
+    } else {
+        t[2] = t[1];  // no value slice: nothing moves for it
+        t[2].first = 0;
+        t[2].bulk_bytes = 0;
+        t[2].head = 0;
+        t[2].tail = 0;
+        t[2].count = 0;
+    }
+    for (int q = lane; q < 16 * NSL; q += 32) {
         const int which = q >> 4;
         const bool tail = ((q >> 3) & 1) != 0;
         const uint32_t e = q & 7;
@@ -291,8 +298,7 @@ __device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, 
         if (!ok) continue;
         const char *src = which == 0 ? reinterpret_cast<const char *>(a.row_end + b.r0)
                                      : (which == 1 ? reinterpret_cast<const char *>(a.idx + b.k0)
-                                                   : static_cast<const char *>(MergeTraits<V, MODE>::third(a)) +
-                                                         static_cast<size_t>(b.k0) * sz);
+                                                   : static_cast<const char *>(a.val) + static_cast<size_t>(b.k0) * sz);
         src += static_cast<size_t>(rel) * sz;
         unsigned char *dst = stage + g_first + rel * sz;
         if (sz == 4)
@@ -315,7 +321,7 @@ __device__ __forceinline__ void produce_tile(const MergeArgs &a, uint64_t *bar, 
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, t[0].bulk_bytes + t[1].bulk_bytes + t[2].bulk_bytes);
 #pragma unroll
-        for (int w = 0; w < 3; ++w)
+        for (int w = 0; w < NSL; ++w)
             if (t[w].bulk_bytes)
                 bulk_g2s(stage + t[w].bulk_off, reinterpret_cast<const void *>(t[w].bulk_src), t[w].bulk_bytes, bar,
                          pol);
@@ -378,7 +384,11 @@ __device__ __forceinline__ void gather_issue(const MergeArgs &a, const unsigned 
     constexpr uint32_t SV = MergeTraits<V, MODE>::SV;
     const unsigned char *val_item0 = stage + h.val_first;  // tile item 0
     const uintptr_t vslot0 = reinterpret_cast<uintptr_t>(val_item0) - static_cast<uintptr_t>(lead) * SV;
-    if (SV == 4) {
+    if (SV == 0) {  // gather-sum: the gathered value is the product
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
+            if (item0 + q >= 0 && item0 + q < nk) vv[q] = 1.f;
+    } else if (SV == 4) {
         int raw[IPT];
         if ((vslot0 & 15u) == 0) {
 #pragma unroll
@@ -399,12 +409,7 @@ __device__ __forceinline__ void gather_issue(const MergeArgs &a, const unsigned 
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
             const int it = item0 + q;
-            if (it >= 0 && it < nk) {
-                if (MODE == kTransposed)
-                    vv[q] = to_f32(__ldg(static_cast<const V *>(a.val) + raw[q]));
-                else
-                    vv[q] = __int_as_float(raw[q]);
-            }
+            if (it >= 0 && it < nk) vv[q] = __int_as_float(raw[q]);
         }
     } else {
         unsigned short raw[IPT];
@@ -834,8 +839,12 @@ cudaError_t dispatch_merge(int mode, int threads, int ipt, const MergeArgs &a, c
             return dispatch_merge_shape<V, kPlain>(threads, ipt, a, st, eb, ea);
         case kBatched:
             return dispatch_merge_shape<V, kBatched>(threads, ipt, a, st, eb, ea);
-        case kTransposed:
-            return dispatch_merge_shape<V, kTransposed>(threads, ipt, a, st, eb, ea);
+        case kGatherSum:
+            // The gathered values are FP32 whatever the matrix's value type: one instance.
+            if constexpr (std::is_same<V, float>::value)
+                return dispatch_merge_shape<V, kGatherSum>(threads, ipt, a, st, eb, ea);
+            else
+                return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;
     }

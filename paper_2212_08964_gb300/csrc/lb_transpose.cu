@@ -10,6 +10,7 @@
 // which every element's rank among equal digits of its block comes from warp match masks.
 // Every step is a pure function of its input, so the plan is bit-exact and deterministic.
 #include <cstdlib>
+#include <cstring>
 
 #include "lb_internal.cuh"
 
@@ -274,34 +275,80 @@ static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, 
     return cudaGetLastError();
 }
 
-// dvalues[k] = g[row(k)] * xg[k] from the forward product's saved gathers: a streaming pass.
-// Per tile, every row end inside the tile adds 1 to a per-slot count in shared memory; the row
-// of a slot is then the inclusive prefix sum of the counts (each thread sums its IPT slots,
-// the block scans the thread totals), so no search is needed.  Slots are aligned so that
-// slot 0 of a tile sits on a 16-byte boundary of xg (the tile's first nonzero at slot `lead`),
-// and each thread moves its IPT consecutive values with vector loads and stores when they all
-// belong to the tile (and dv has xg's alignment).
-template <int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) dvalues_saved_kernel(int G, int m, const int *__restrict__ tile_row,
-                                                                const int *__restrict__ tile_nz,
-                                                                const int *__restrict__ row_end,
-                                                                const float *__restrict__ g,
-                                                                const float *__restrict__ xg, float *__restrict__ dv) {
+// One streaming pass over the nonzeros in CSR order, tile by tile over the forward partition:
+//   pv[pos(k)] = values[k] * g[row(k)]   (pos = bucket_pos, or the identity), when pv is given;
+//   dv[k]      = g[row(k)] * xg[k]        (the values gradient from saved gathers), when dv is.
+// The rows come without any search: every row end inside the tile adds 1 to a per-slot count
+// in shared memory, and a slot's row is the inclusive prefix sum of the counts (each thread
+// sums its IPT slots, the block scans the thread totals).  Slot 0 of a tile sits 16 bytes
+// aligned in the nonzero arrays (the tile's first nonzero at slot `lead`), so each thread
+// moves its IPT consecutive entries with vector loads and stores where the arrays allow.  The
+// scaled values go to shared memory and out in a second, lane-consecutive pass, so that the
+// scattered bucket positions of neighbouring nonzeros coalesce as well as they can.
+template <typename V, int IPT>
+__device__ __forceinline__ void load_values(const V *src, bool vec, bool full, int j0, int nk, float (&o)[IPT]) {
+    if (full && vec) {
+        if constexpr (sizeof(V) == 4) {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4) {
+                const float4 t = __ldcs(reinterpret_cast<const float4 *>(src + q));
+                o[q] = t.x;
+                o[q + 1] = t.y;
+                o[q + 2] = t.z;
+                o[q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4) {
+                const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(src + q));
+                const uint32_t w[2] = {t.x, t.y};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    V lo, hi;
+                    const unsigned short bl = static_cast<unsigned short>(w[e] & 0xffffu);
+                    const unsigned short bh = static_cast<unsigned short>(w[e] >> 16);
+                    memcpy(&lo, &bl, 2);
+                    memcpy(&hi, &bh, 2);
+                    o[q + 2 * e] = to_f32(lo);
+                    o[q + 2 * e + 1] = to_f32(hi);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) o[q] = (j0 + q >= 0 && j0 + q < nk) ? to_f32(src[q]) : 0.f;
+    }
+}
+
+template <typename V, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, const int *__restrict__ tile_row,
+                                                               const int *__restrict__ tile_nz,
+                                                               const int *__restrict__ row_end,
+                                                               const float *__restrict__ g,
+                                                               const V *__restrict__ values,
+                                                               const int *__restrict__ bucket_pos,
+                                                               float *__restrict__ pv, const float *__restrict__ xg,
+                                                               float *__restrict__ dv) {
     constexpr int T = THREADS * IPT;
     constexpr int WARPS = THREADS / 32;
     static_assert(IPT % 4 == 0, "slots move four at a time");
     __shared__ __align__(16) int cnt[T];
+    __shared__ __align__(16) float s_pv[T];
     __shared__ int wsum[WARPS];
     for (int i = threadIdx.x; i < T; i += THREADS) cnt[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool vec_dv = ((reinterpret_cast<uintptr_t>(dv) - reinterpret_cast<uintptr_t>(xg)) & 15u) == 0;
-    const int xg_word = static_cast<int>((reinterpret_cast<uintptr_t>(xg) >> 2) & 3u);
+    const bool want_pv = pv != nullptr, want_dv = dv != nullptr;
+    // Slot 0 of every tile is 16-byte aligned in an array whose base is (4-byte elements) or
+    // 8-byte aligned (2-byte values, moved four at a time).
+    const bool vec_xg = (reinterpret_cast<uintptr_t>(xg) & 15u) == 0;
+    const bool vec_dv = (reinterpret_cast<uintptr_t>(dv) & 15u) == 0;
+    const bool vec_v = (reinterpret_cast<uintptr_t>(values) & (sizeof(V) == 4 ? 15u : 7u)) == 0;
     for (int tile = blockIdx.x; tile < G; tile += gridDim.x) {
         const int r0 = __ldg(tile_row + tile), r1 = __ldg(tile_row + tile + 1);
         const int k0 = __ldg(tile_nz + tile), k1 = __ldg(tile_nz + tile + 1);
         const int nr = r1 - r0, nk = k1 - k0;
-        const int lead = (xg_word + k0) & 3;  // xg + k0 - lead is 16-byte aligned
+        const int lead = k0 & 3;  // nonzero k0 - lead is a multiple of 4
         if (nr < 0 || nk < 0 || nk + lead > T) continue;  // malformed offsets (block-uniform)
         for (int r = threadIdx.x; r < nr; r += THREADS) {
             const int e = __ldg(row_end + r0 + r) - k0;  // first nonzero of the next row, tile-local
@@ -335,40 +382,88 @@ __global__ void __launch_bounds__(THREADS) dvalues_saved_kernel(int G, int m, co
         const int j0 = s0 - lead;  // tile item of this thread's first slot
         if (j0 + IPT > 0 && j0 < nk) {
             const bool full = j0 >= 0 && j0 + IPT <= nk;
-            const float *src = xg + k0 + j0;
-            float *dst = dv + k0 + j0;
-            float xv[IPT];
-            if (full) {
-#pragma unroll
-                for (int q = 0; q < IPT; q += 4) {
-                    const float4 t = __ldcs(reinterpret_cast<const float4 *>(src + q));
-                    xv[q] = t.x;
-                    xv[q + 1] = t.y;
-                    xv[q + 2] = t.z;
-                    xv[q + 3] = t.w;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) xv[q] = (j0 + q >= 0 && j0 + q < nk) ? __ldcs(src + q) : 0.f;
-            }
-            float o[IPT];
+            float gq[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 const int row = r0 + base + c[q];
-                o[q] = (j0 + q >= 0 && j0 + q < nk && row < m) ? __ldg(g + row) * xv[q] : 0.f;
+                gq[q] = (j0 + q >= 0 && j0 + q < nk && row < m) ? __ldg(g + row) : 0.f;
             }
-            if (full && vec_dv) {
+            if (want_pv) {
+                float vv[IPT];
+                load_values<V, IPT>(values + k0 + j0, vec_v, full, j0, nk, vv);
 #pragma unroll
                 for (int q = 0; q < IPT; q += 4)
-                    __stcs(reinterpret_cast<float4 *>(dst + q), make_float4(o[q], o[q + 1], o[q + 2], o[q + 3]));
-            } else {
+                    *reinterpret_cast<float4 *>(s_pv + s0 + q) =
+                        make_float4(vv[q] * gq[q], vv[q + 1] * gq[q + 1], vv[q + 2] * gq[q + 2], vv[q + 3] * gq[q + 3]);
+            }
+            if (want_dv) {
+                float xv[IPT];
+                load_values<float, IPT>(xg + k0 + j0, vec_xg, full, j0, nk, xv);
+                float *dst = dv + k0 + j0;
+                if (full && vec_dv) {
 #pragma unroll
-                for (int q = 0; q < IPT; ++q)
-                    if (j0 + q >= 0 && j0 + q < nk) __stcs(dst + q, o[q]);
+                    for (int q = 0; q < IPT; q += 4)
+                        __stcs(reinterpret_cast<float4 *>(dst + q),
+                               make_float4(gq[q] * xv[q], gq[q + 1] * xv[q + 1], gq[q + 2] * xv[q + 2],
+                                           gq[q + 3] * xv[q + 3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if (j0 + q >= 0 && j0 + q < nk) __stcs(dst + q, gq[q] * xv[q]);
+                }
             }
         }
-        __syncthreads();  // wsum and the counts are reused by the next tile
+        if (want_pv) {
+            __syncthreads();
+            for (int j = threadIdx.x; j < nk; j += THREADS) {
+                const int k = k0 + j;
+                const int dst = bucket_pos != nullptr ? __ldcs(bucket_pos + k) : k;
+                pv[dst] = s_pv[j + lead];
+            }
+        }
+        __syncthreads();  // the counts, wsum and s_pv are reused by the next tile
     }
+}
+
+template <typename V>
+static cudaError_t launch_csr_backward_t(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
+                                         const int *row_end, const float *g, const V *values, const int *bucket_pos,
+                                         float *pv, const float *xg, float *dv, cudaStream_t stream) {
+    long long grid = static_cast<long long>(current_sm_count()) * 6;
+    // A tile's slots: its items plus a lead of up to 3 must fit.
+    if (tile_items + 3 <= 2048) {
+        if (grid > num_tiles) grid = num_tiles;
+        csr_backward_kernel<V, 256, 8><<<static_cast<int>(grid), 256, 0, stream>>>(
+            num_tiles, m, tile_row, tile_nz, row_end, g, values, bucket_pos, pv, xg, dv);
+    } else if (tile_items + 3 <= 4096) {
+        grid /= 2;
+        if (grid > num_tiles) grid = num_tiles;
+        csr_backward_kernel<V, 512, 8><<<static_cast<int>(grid), 512, 0, stream>>>(
+            num_tiles, m, tile_row, tile_nz, row_end, g, values, bucket_pos, pv, xg, dv);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+                                const int *tile_nz, const int *row_end, const float *g, const void *values,
+                                const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream) {
+    if (num_tiles <= 0) return cudaSuccess;
+    if ((pv != nullptr && values == nullptr) || (dv != nullptr && xg == nullptr)) return cudaErrorInvalidValue;
+    switch (vdt) {
+        case LB_F32:
+            return launch_csr_backward_t<float>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                static_cast<const float *>(values), bucket_pos, pv, xg, dv, stream);
+        case LB_BF16:
+            return launch_csr_backward_t<__nv_bfloat16>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                        static_cast<const __nv_bfloat16 *>(values), bucket_pos, pv,
+                                                        xg, dv, stream);
+        case LB_F16:
+            return launch_csr_backward_t<__half>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                 static_cast<const __half *>(values), bucket_pos, pv, xg, dv, stream);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dvalues(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
@@ -377,23 +472,8 @@ cudaError_t launch_dvalues(int num_tiles, int m, int tile_items, const int *tile
     if (xg == nullptr)
         return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, dv, nullptr,
                                        stream);
-    if (num_tiles <= 0) return cudaSuccess;
-    if ((reinterpret_cast<uintptr_t>(xg) & 3u) != 0) return cudaErrorInvalidValue;  // float arrays
-    // A tile's slots: its items plus a lead of up to 3 must fit.
-    long long grid = static_cast<long long>(current_sm_count()) * 8;
-    if (tile_items + 3 <= 2048) {
-        if (grid > num_tiles) grid = num_tiles;
-        dvalues_saved_kernel<256, 8><<<static_cast<int>(grid), 256, 0, stream>>>(num_tiles, m, tile_row, tile_nz,
-                                                                                 row_end, g, xg, dv);
-    } else if (tile_items + 3 <= 4096) {
-        grid /= 2;
-        if (grid > num_tiles) grid = num_tiles;
-        dvalues_saved_kernel<512, 8><<<static_cast<int>(grid), 512, 0, stream>>>(num_tiles, m, tile_row, tile_nz,
-                                                                                 row_end, g, xg, dv);
-    } else {
-        return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return launch_csr_backward(LB_F32, num_tiles, m, tile_items, tile_row, tile_nz, row_end, g, nullptr, nullptr,
+                               nullptr, xg, dv, stream);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -459,16 +539,16 @@ done:
 }
 
 // ------------------------------------------------------------------------------------------
-// Bringing CSR-ordered values into CSC order, every call, without random HBM reads.
+// Bringing CSR-ordered data into CSC order, every call, without random HBM accesses.
 //
-// The transposed product needs, for CSC entry p, the value of CSR entry perm[p]: a random
+// The transposed product needs, for CSC entry p, data of CSR entry perm[p]: a random
 // permutation of an array far larger than L2.  Gathering it directly costs one DRAM sector
 // per nonzero.  Instead the CSC entries are cut into buckets of 2^shift consecutive entries
-// (each bucket's values fit comfortably in L2), and each call (1) streams the values once in
-// CSR order into bucket order -- CSR entries of one bucket keep their CSR order, so every
-// bucket receives one sequential stream of writes -- and (2) lets the transposed kernel
-// gather from the bucket being worked on, which stays resident in L2 while the persistent
-// CTAs sweep through it.  Both maps are fixed per structure, so results stay deterministic.
+// (each bucket's data fit comfortably in L2), and each call (1) streams the CSR-ordered data
+// once into bucket order -- CSR entries of one bucket keep their CSR order, so every bucket
+// receives one sequential stream of writes -- and (2) lets the transposed kernel gather from
+// the bucket being worked on, which stays resident in L2 while the persistent CTAs sweep
+// through it.  Both maps are fixed per structure, so results stay deterministic.
 
 int value_bucket_shift(long long nnz) {
     int shift = 23;  // 8M entries: 32 MB of FP32 values
@@ -516,31 +596,6 @@ cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket
     }
     cudaError_t e2 = cudaFreeAsync(work, st);
     return e != cudaSuccess ? e : e2;
-}
-
-template <typename E>
-__global__ void __launch_bounds__(256) bucket_values_kernel(int nnz, const E *__restrict__ v,
-                                                            const int *__restrict__ pos, E *__restrict__ tmp) {
-    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < nnz;
-         k += static_cast<long long>(gridDim.x) * blockDim.x)
-        tmp[__ldg(pos + k)] = __ldg(v + k);
-}
-
-cudaError_t launch_bucket_values(int nnz, int elem_bytes, const void *values, const int *bucket_pos, void *tmp,
-                                 cudaStream_t st) {
-    if (nnz <= 0) return cudaSuccess;
-    long long blocks = (static_cast<long long>(nnz) + 255) / 256;
-    const long long cap = static_cast<long long>(current_sm_count()) * 32;
-    if (blocks > cap) blocks = cap;
-    if (elem_bytes == 4)
-        bucket_values_kernel<int><<<static_cast<int>(blocks), 256, 0, st>>>(nnz, static_cast<const int *>(values),
-                                                                          bucket_pos, static_cast<int *>(tmp));
-    else if (elem_bytes == 2)
-        bucket_values_kernel<unsigned short><<<static_cast<int>(blocks), 256, 0, st>>>(
-            nnz, static_cast<const unsigned short *>(values), bucket_pos, static_cast<unsigned short *>(tmp));
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
 }
 
 }  // namespace lb

@@ -105,6 +105,7 @@ def _declare(lib):
         "lb_spmv_dvalues": [_P, _P, _P, _P, _P, _P],
         "lb_spmv_planned_save": [_P, _P, _P, _I, _P, _P, _P, _P],
         "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _P],
+        "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -334,6 +335,20 @@ class Plan:
         _check(_lib.lb_spmv_dvalues(self._h, _ptr(col_idx), _ptr(g), _ptr(x), _ptr(dv), _stream(stream)), "lb_spmv_dvalues")
         return dv
 
+    def backward(self, values, g, x_gathered, dx=None, dvalues=None, stream=None):
+        """(dx, dvalues) = (A^T g, g[row] * x_gathered) in two passes (lb_spmv_backward);
+        needs ``build_transpose`` and x gathers saved by ``spmv(save_gathered=...)``."""
+        _need(values, None, "values", self.nnz)
+        _need(g, torch.float32, "g", self.m)
+        _need(x_gathered, torch.float32, "x_gathered", self.nnz)
+        dx = torch.empty(self.n, dtype=torch.float32, device=g.device) if dx is None else dx
+        dvalues = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if dvalues is None else dvalues
+        _need(dx, torch.float32, "dx", self.n)
+        _need(dvalues, torch.float32, "dvalues", self.nnz)
+        _check(_lib.lb_spmv_backward(self._h, _ptr(values), _vdt(values), _ptr(g), _ptr(x_gathered), _ptr(dx),
+                                     _ptr(dvalues), _stream(stream)), "lb_spmv_backward")
+        return dx, dvalues
+
     def dvalues_gathered(self, g, x_gathered, out=None, stream=None) -> torch.Tensor:
         """dvalues[k] = g[row(k)] * x_gathered[k] (x gathers saved by ``spmv(save_gathered=...)``)."""
         _need(g, torch.float32, "g", self.m)
@@ -420,7 +435,8 @@ class SpMV(torch.autograd.Function):
     Backward: dx = A^T g by merge-path over the plan's CSC view (built on first use),
     dvalues = g[row] * x[col] per nonzero over the forward partition.  When the values need a
     gradient and the plan is merge-path, the forward saves x[col] of every nonzero (4 bytes per
-    nonzero) and the backward streams them back instead of gathering x again.
+    nonzero) and the backward streams them back instead of gathering x again; with both
+    gradients wanted, one pass over the nonzeros forms dvalues and the scaled values for dx.
     """
 
     @staticmethod
@@ -438,14 +454,17 @@ class SpMV(torch.autograd.Function):
         plan = ctx.plan
         g = g.contiguous().float()
         dvals = dx = None
-        if ctx.needs_input_grad[0]:
-            dvals = plan.dvalues(col_idx, g, x.detach()) if xg is None else plan.dvalues_gathered(g, xg)
-            if values.dtype != torch.float32:
-                dvals = dvals.to(values.dtype)
-        if ctx.needs_input_grad[1]:
-            if not plan.has_transpose:
-                plan.build_transpose(col_idx)
-            dx = plan.spmv_t(values.detach(), g)
+        if ctx.needs_input_grad[1] and not plan.has_transpose:
+            plan.build_transpose(col_idx)
+        if ctx.needs_input_grad[0] and ctx.needs_input_grad[1] and xg is not None:
+            dx, dvals = plan.backward(values.detach(), g, xg)  # both in two passes
+        else:
+            if ctx.needs_input_grad[0]:
+                dvals = plan.dvalues(col_idx, g, x.detach()) if xg is None else plan.dvalues_gathered(g, xg)
+            if ctx.needs_input_grad[1]:
+                dx = plan.spmv_t(values.detach(), g)
+        if dvals is not None and values.dtype != torch.float32:
+            dvals = dvals.to(values.dtype)
         return dvals, dx, None, None
 
 

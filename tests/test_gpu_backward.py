@@ -106,6 +106,61 @@ def test_saved_gathers_unaligned_views(lb, orc):
         assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
 
 
+@pytest.mark.parametrize("name", ["worked", "powerlaw_4k", "skew", "wide", "stencil_small"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("bucket_shift", [None, "10"])
+def test_two_pass_backward(lb, orc, monkeypatch, name, dtype, bucket_shift):
+    """lb_spmv_backward: dx and dvalues from one CSR-order pass plus the gather-sum, equal bit
+    for bit to lb_spmv_t and lb_spmv_dvalues_gathered, and to the oracle within tolerance."""
+    if bucket_shift:
+        monkeypatch.setenv("LBSPMV_VALUE_BUCKET_SHIFT", bucket_shift)
+    a = _cases()[name]
+    plan, ci, v = _plan_with_t(lb, a, dtype=dtype)
+    x = vec(a.n, 211)
+    g = vec(a.m, 212)
+    xg = torch.empty(a.nnz, device="cuda")
+    plan.spmv(ci, v, dev(x), save_gathered=xg)
+    dx, dv = plan.backward(v, dev(g), xg)
+    dx2 = plan.spmv_t(v, dev(g))
+    dv2 = plan.dvalues_gathered(dev(g), xg)
+    torch.cuda.synchronize()
+    assert torch.equal(dx, dx2) and torch.equal(dv, dv2)
+    vals = a.values if dtype == torch.float32 else rounded(a.values, dtype)
+    check_bound(dx.cpu().numpy(), orc.spmv_t(a.row_offsets, a.col_idx, vals, g, a.n),
+                orc.col_absdot(a.row_offsets, a.col_idx, vals, g, a.n), TOL32, "columns")
+    assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+
+
+def test_two_pass_backward_unaligned_views(lb, orc):
+    """Values, saved gathers and dvalues at element offsets that break 16-byte alignment."""
+    a = workload("powerlaw_4k")
+    x = vec(a.n, 213)
+    g = vec(a.m, 214)
+    ro, ci, _ = to_dev(a)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    plan.build_transpose(ci)
+    ref_dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
+    scale = orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n)
+    ref_dv = orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32)
+    for dtype in (torch.float32, torch.bfloat16):
+        for off_v, off_x, off_d in [(1, 0, 0), (0, 2, 0), (0, 0, 3), (3, 1, 2)]:
+            vb = torch.zeros(a.nnz + 4, dtype=dtype, device="cuda")
+            vb[off_v: off_v + a.nnz] = dev(a.values, dtype)
+            v = vb[off_v: off_v + a.nnz]
+            xgb = torch.zeros(a.nnz + 4, device="cuda")
+            xg = xgb[off_x: off_x + a.nnz]
+            dvb = torch.full((a.nnz + 4,), float("nan"), device="cuda")
+            dvv = dvb[off_d: off_d + a.nnz]
+            plan.spmv(ci, v, dev(x), save_gathered=xg)
+            dx, _ = plan.backward(v, dev(g), xg, dvalues=dvv)
+            torch.cuda.synchronize()
+            assert np.array_equal(dvv.cpu().numpy(), ref_dv)
+            assert torch.isnan(dvb[:off_d]).all() and torch.isnan(dvb[off_d + a.nnz:]).all()
+            vals = a.values if dtype == torch.float32 else rounded(a.values, dtype)
+            check_bound(dx.cpu().numpy(), orc.spmv_t(a.row_offsets, a.col_idx, vals, g, a.n),
+                        orc.col_absdot(a.row_offsets, a.col_idx, vals, g, a.n), TOL32, "columns")
+
+
 @pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped"])
 def test_autograd_function(lb, orc, sched):
     a = workload("powerlaw_4k")
@@ -182,8 +237,7 @@ def test_full_size_powerlaw_4m_backward(lb, orc):
     g = vec(a.m, 3)
     xg = torch.empty(a.nnz, device="cuda")
     y = plan.spmv(ci, v, dev(x), save_gathered=xg)
-    dx = plan.spmv_t(v, dev(g))
-    dv = plan.dvalues_gathered(dev(g), xg)
+    dx, dv = plan.backward(v, dev(g), xg)
     dv2 = plan.dvalues(ci, dev(g), dev(x))
     torch.cuda.synchronize()
     ref_y = orc.spmv(a.row_offsets, a.col_idx, a.values, x)
