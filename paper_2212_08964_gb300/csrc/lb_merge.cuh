@@ -48,8 +48,9 @@ namespace lb {
 
 // Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.  SV is
 // the size of the third staged array (values, or CSR positions for the transposed product);
-// NS is the number of shared-memory stages, NB the number of product buffers.
-template <int GW, int IPT, int SV, int NS, int NB>
+// NS is the number of shared-memory stages, NB the number of product buffers, RB the register
+// budget per thread that sets the resident CTAs per SM.
+template <int GW, int IPT, int SV, int NS, int NB, int RB>
 struct MergeShape {
     static_assert(IPT == 8 || IPT == 16, "items per thread: 8 or 16 (one byte or halfword of flags)");
     static constexpr int GT = GW * 32;   // gather threads
@@ -76,9 +77,9 @@ struct MergeShape {
     static constexpr int NBUF = NB;
     static constexpr size_t SMEM = HDR + NSTAGE * static_cast<size_t>(STAGE) + BITS + NBUF * BUF;
     // Resident CTAs per SM from shared memory (228 KB per SM, 1 KB reserved per CTA), capped
-    // by a register budget of 56 per thread.
+    // by the register budget.
     static constexpr int BY_SMEM = static_cast<int>((228 * 1024) / (SMEM + 1024));
-    static constexpr int BY_REGS = 65536 / (THREADS * 56);
+    static constexpr int BY_REGS = 65536 / (THREADS * RB);
     static constexpr int MIN_BLOCKS_RAW = BY_SMEM < BY_REGS ? BY_SMEM : BY_REGS;
     static constexpr int MIN_BLOCKS = MIN_BLOCKS_RAW < 1 ? 1 : MIN_BLOCKS_RAW;
 };
@@ -170,6 +171,7 @@ struct MergeTraits {
     static constexpr int NSLICE = SV > 0 ? 3 : 2;  // staged arrays: row ends, indices[, values]
     static constexpr int NS = 3;                   // stages
     static constexpr int NB = 2;                   // product buffers
+    static constexpr int RB = 56;                  // registers per thread
 };
 
 // A tile from a valid partition has rows + atoms <= TILE_ITEMS; anything else means the
@@ -548,10 +550,10 @@ __device__ __forceinline__ bool group_bar_any(bool pred) {
 }
 
 template <typename V, int GW, int IPT, int MODE>
-__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>::THREADS,
-                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>::MIN_BLOCKS)
+__global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB, MergeTraits<V, MODE>::RB>::THREADS,
+                                  MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB, MergeTraits<V, MODE>::RB>::MIN_BLOCKS)
     merge_spmv_kernel(const MergeArgs a) {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB, MergeTraits<V, MODE>::RB>;
     constexpr int NS = Sh::NSTAGE;
     constexpr int NB = Sh::NBUF;
     static_assert(NB >= 1 && NB <= 2, "one or two product buffers");
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
 // device; also raises the kernel's dynamic shared-memory limit).
 template <typename V, int GW, int IPT, int MODE>
 int merge_blocks_per_sm() {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB, MergeTraits<V, MODE>::RB>;
     constexpr int kMaxDev = 64;
     static int cache[kMaxDev] = {0};
     static std::mutex mu;
@@ -804,7 +806,7 @@ int merge_blocks_per_sm() {
 
 template <typename V, int GW, int IPT, int MODE>
 cudaError_t launch_merge_cfg(const MergeArgs &a, cudaStream_t st, cudaEvent_t eb, cudaEvent_t ea) {
-    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB>;
+    using Sh = MergeShape<GW, IPT, static_cast<int>(MergeTraits<V, MODE>::SV), MergeTraits<V, MODE>::NS, MergeTraits<V, MODE>::NB, MergeTraits<V, MODE>::RB>;
     const int per_sm = merge_blocks_per_sm<V, GW, IPT, MODE>();
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const long long wave = static_cast<long long>(per_sm) * current_sm_count();

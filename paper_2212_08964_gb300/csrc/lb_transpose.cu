@@ -350,12 +350,29 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
         const int nr = r1 - r0, nk = k1 - k0;
         const int lead = k0 & 3;  // nonzero k0 - lead is a multiple of 4
         if (nr < 0 || nk < 0 || nk + lead > T) continue;  // malformed offsets (block-uniform)
+        const int s0 = threadIdx.x * IPT;
+        const int j0 = s0 - lead;  // tile item of this thread's first slot
+        const bool mine = j0 + IPT > 0 && j0 < nk;
+        const bool full = j0 >= 0 && j0 + IPT <= nk;
+        // Every load that does not depend on the rows goes out first, so its latency overlaps
+        // the row-end staging and the scan: this thread's values and saved gathers (blocked)
+        // and the bucket positions of the lane-consecutive scatter.
+        float vv[IPT], xv[IPT];
+        int bp[IPT];
+        if (want_pv && mine) load_values<V, IPT>(values + k0 + j0, vec_v, full, j0, nk, vv);
+        if (want_dv && mine) load_values<float, IPT>(xg + k0 + j0, vec_xg, full, j0, nk, xv);
+        if (want_pv) {
+#pragma unroll
+            for (int u = 0; u < IPT; ++u) {
+                const int j = threadIdx.x + u * THREADS;
+                bp[u] = j < nk ? (bucket_pos != nullptr ? __ldcs(bucket_pos + k0 + j) : k0 + j) : 0;
+            }
+        }
         for (int r = threadIdx.x; r < nr; r += THREADS) {
             const int e = __ldg(row_end + r0 + r) - k0;  // first nonzero of the next row, tile-local
             if (e >= 0 && e < nk) atomicAdd(&cnt[e + lead], 1);
         }
         __syncthreads();
-        const int s0 = threadIdx.x * IPT;
         int c[IPT];
 #pragma unroll
         for (int q = 0; q < IPT; q += 4) {
@@ -379,9 +396,7 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
         __syncthreads();
         int base = incl - tot;
         for (int w = 0; w < warp; ++w) base += wsum[w];
-        const int j0 = s0 - lead;  // tile item of this thread's first slot
-        if (j0 + IPT > 0 && j0 < nk) {
-            const bool full = j0 >= 0 && j0 + IPT <= nk;
+        if (mine) {
             float gq[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
@@ -389,16 +404,12 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
                 gq[q] = (j0 + q >= 0 && j0 + q < nk && row < m) ? __ldg(g + row) : 0.f;
             }
             if (want_pv) {
-                float vv[IPT];
-                load_values<V, IPT>(values + k0 + j0, vec_v, full, j0, nk, vv);
 #pragma unroll
                 for (int q = 0; q < IPT; q += 4)
                     *reinterpret_cast<float4 *>(s_pv + s0 + q) =
                         make_float4(vv[q] * gq[q], vv[q + 1] * gq[q + 1], vv[q + 2] * gq[q + 2], vv[q + 3] * gq[q + 3]);
             }
             if (want_dv) {
-                float xv[IPT];
-                load_values<float, IPT>(xg + k0 + j0, vec_xg, full, j0, nk, xv);
                 float *dst = dv + k0 + j0;
                 if (full && vec_dv) {
 #pragma unroll
@@ -415,10 +426,10 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
         }
         if (want_pv) {
             __syncthreads();
-            for (int j = threadIdx.x; j < nk; j += THREADS) {
-                const int k = k0 + j;
-                const int dst = bucket_pos != nullptr ? __ldcs(bucket_pos + k) : k;
-                pv[dst] = s_pv[j + lead];
+#pragma unroll
+            for (int u = 0; u < IPT; ++u) {
+                const int j = threadIdx.x + u * THREADS;
+                if (j < nk) pv[bp[u]] = s_pv[j + lead];
             }
         }
         __syncthreads();  // the counts, wsum and s_pv are reused by the next tile
@@ -429,21 +440,21 @@ template <typename V>
 static cudaError_t launch_csr_backward_t(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
                                          const int *row_end, const float *g, const V *values, const int *bucket_pos,
                                          float *pv, const float *xg, float *dv, cudaStream_t stream) {
-    long long grid = static_cast<long long>(current_sm_count()) * 6;
-    // A tile's slots: its items plus a lead of up to 3 must fit.
-    if (tile_items + 3 <= 2048) {
+    // One wave of resident CTAs (the kernel loops over tiles).  A tile's slots: its items plus
+    // a lead of up to 3 must fit.
+    auto launch = [&](auto kern, int threads) -> cudaError_t {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+        if (e != cudaSuccess) return e;
+        long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
         if (grid > num_tiles) grid = num_tiles;
-        csr_backward_kernel<V, 256, 8><<<static_cast<int>(grid), 256, 0, stream>>>(
-            num_tiles, m, tile_row, tile_nz, row_end, g, values, bucket_pos, pv, xg, dv);
-    } else if (tile_items + 3 <= 4096) {
-        grid /= 2;
-        if (grid > num_tiles) grid = num_tiles;
-        csr_backward_kernel<V, 512, 8><<<static_cast<int>(grid), 512, 0, stream>>>(
-            num_tiles, m, tile_row, tile_nz, row_end, g, values, bucket_pos, pv, xg, dv);
-    } else {
-        return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+        kern<<<static_cast<int>(grid), threads, 0, stream>>>(num_tiles, m, tile_row, tile_nz, row_end, g, values,
+                                                             bucket_pos, pv, xg, dv);
+        return cudaGetLastError();
+    };
+    if (tile_items + 3 <= 2048) return launch(csr_backward_kernel<V, 256, 8>, 256);
+    if (tile_items + 3 <= 4096) return launch(csr_backward_kernel<V, 512, 8>, 512);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
