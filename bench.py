@@ -54,7 +54,9 @@ def parse_args(argv=None):
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    p.add_argument("--extras", action="store_true", help="also time batched-vs-plain and BF16-vs-FP32")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the secondary lines (BF16/FP16 step, batched vs per-matrix)")
+    p.add_argument("--extras", action="store_true", help="also time the 8M-row matrix in FP32, BF16 and FP16")
     return p.parse_args(argv)
 
 
@@ -466,6 +468,21 @@ def run_ours(args):
         result["e2e"] = {"value": total_b * world / (e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke}
 
+    if rank == 0 and not args.no_secondary:
+        # The metric's second half: BF16/FP16 values against FP32 on this step, and the batched
+        # form (one persistent launch in a CUDA graph) against one call per matrix.
+        def step_ms(vals):
+            return _time(torch, lambda: step(vals, xd, gd), 20)
+
+        f32_ms = step_ms(v)
+        mixed = {"f32_step_ms": f32_ms}
+        for name, dt, vbytes in (("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
+            ms_ = step_ms(v.to(dt))
+            mixed[f"{name}_step_ms"] = ms_
+            mixed[f"{name}_speedup_vs_f32"] = f32_ms / ms_
+        mixed["stencil7_160_forward"] = run_stencil_precision(lb, torch, dev)
+        result["mixed_precision"] = mixed
+        result["batched"] = run_batched(lb, torch, dev)
     if args.extras and rank == 0:
         result["extras"] = run_extras(lb, torch, dev)
 
@@ -482,47 +499,91 @@ def run_ours(args):
 
 
 def run_extras(lb, torch, dev):
-    """Batched vs per-matrix plain calls, and BF16/FP16 values vs FP32 values."""
+    """The 8M-row power-law matrix (128M nonzeros): forward and the full step with FP32, BF16
+    and FP16 values."""
     from paper_2212_08964_gb300 import synth
 
     out = {}
-    # BF16 / FP16 vs FP32 values on the 8M-row power-law matrix (forward only).
     a = synth.workload("powerlaw_8m")
-    x = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(6), a.n)).to(dev)
+    rng = np.random.default_rng(6)
+    x = torch.from_numpy(synth.uniform_pm1(rng, a.n)).to(dev)
+    g = torch.from_numpy(synth.uniform_pm1(rng, a.m)).to(dev)
     ro, ci = torch.from_numpy(a.row_offsets).to(dev), torch.from_numpy(a.col_idx).to(dev)
     plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    plan.build_transpose(ci)
     y = torch.empty(a.m, device=dev)
+    dx = torch.empty(a.n, device=dev)
+    dv = torch.empty(a.nnz, device=dev)
+    xg = torch.empty(a.nnz, device=dev)
     for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
         v = torch.from_numpy(a.values).to(dev).to(dt)
         ms = _time(torch, lambda: plan.spmv(ci, v, x, out=y), 20)
-        out[f"powerlaw_8m_{name}"] = {"ms": ms, "GB/s": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9}
-    del plan, v, ci, ro
-    # Batched (one launch, CUDA graph) vs one planned call per matrix.
+
+        def full():
+            plan.spmv(ci, v, x, out=y, save_gathered=xg)
+            plan.backward(v, g, xg, dx=dx, dvalues=dv)
+
+        ms_step = _time(torch, full, 10)
+        out[f"powerlaw_8m_{name}"] = {"forward_ms": ms, "forward_GBps": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9,
+                                      "step_ms": ms_step}
+    return out
+
+
+def run_stencil_precision(lb, torch, dev):
+    """The balanced contrast: the 7-point stencil on a 160^3 grid (4.1M rows, 28.5M nonzeros),
+    whose gathers hit neighbouring sectors, so the pass is bound by streaming the matrix and
+    narrower values pay off.  Forward with FP32, BF16 and FP16 values, thread-mapped (the
+    schedule the autotuner picks for this class) and merge-path."""
+    from paper_2212_08964_gb300 import synth
+
+    a = synth.workload("stencil7_160")
+    x = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(3), a.n)).to(dev)
+    ro, ci = torch.from_numpy(a.row_offsets).to(dev), torch.from_numpy(a.col_idx).to(dev)
+    y = torch.empty(a.m, device=dev)
+    out = {"workload": f"stencil7_160: m = n = {a.m}, nnz = {a.nnz}"}
+    for sched in ("thread_mapped", "merge_path"):
+        plan = lb.Plan(ro, a.n, a.nnz, schedule=sched)
+        for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
+            v = torch.from_numpy(a.values).to(dev).to(dt)
+            ms = _time(torch, lambda: plan.spmv(ci, v, x, out=y), 30)
+            out[f"{sched}_{name}"] = {"ms": ms, "GBps": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9}
+        out[f"{sched}_bf16_speedup_vs_f32"] = out[f"{sched}_f32"]["ms"] / out[f"{sched}_bf16"]["ms"]
+    return out
+
+
+def run_batched(lb, torch, dev):
+    """4096 matrices of uneven size: one persistent launch replayed from a CUDA graph against one
+    planned call per matrix (the plain per-matrix form)."""
+    from paper_2212_08964_gb300 import synth
+
+    out = {}
     b = synth.workload("batched_4096")
     xs = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(5), int(b.ns.sum()))).to(dev)
     bci, bv = torch.from_numpy(b.col_idx).to(dev), torch.from_numpy(b.values).to(dev)
     bro = torch.from_numpy(b.row_offsets).to(dev)
     bp = lb.BatchedPlan(b.ms, b.ns, b.nnzs, bro)
     yb = torch.empty(int(b.ms.sum()), device=dev)
-    bp.spmv(bci, bv, xs, out=yb)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        bp.spmv(bci, bv, xs, out=yb)
+        bp.spmv(bci, bv, xs, out=yb)  # first call outside the capture (kernel attributes)
     torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         bp.spmv(bci, bv, xs, out=yb)
     ms_b = _time(torch, graph.replay, 20)
     total = sum(spmv_bytes(int(m), int(n), int(z)) for m, n, z in zip(b.ms, b.ns, b.nnzs))
-    out["batched_4096_graph"] = {"ms": ms_b, "GB/s": total / (ms_b * 1e-3) / 1e9, "launches": 2}
-    # Per-matrix plans, one call each.
+    info = bp.info()
+    out["workload"] = f"batched_4096: {b.count} matrices, {int(b.ms.sum())} rows, {int(b.nnzs.sum())} nonzeros"
+    out["graph_ms"] = ms_b
+    out["graph_GBps"] = total / (ms_b * 1e-3) / 1e9
+    out["graph_launches"] = 2
+    out["shape"] = [info["threads"], info["items_per_thread"]]
     plans, views = [], []
     ro_pos = nz_pos = x_pos = y_pos = 0
     for i in range(b.count):
         m, n, z = int(b.ms[i]), int(b.ns[i]), int(b.nnzs[i])
-        p = lb.Plan(bro[ro_pos: ro_pos + m + 1], n, z, schedule="merge_path")
+        p = lb.Plan(bro[ro_pos: ro_pos + m + 1], n, z, schedule="auto")
         plans.append(p)
         views.append((bci[nz_pos: nz_pos + z], bv[nz_pos: nz_pos + z], xs[x_pos: x_pos + n], yb[y_pos: y_pos + m]))
         ro_pos += m + 1
@@ -535,8 +596,10 @@ def run_extras(lb, torch, dev):
             p.spmv(c_, v_, x_, out=y_)
 
     ms_p = _time(torch, per_matrix, 3)
-    out["batched_4096_per_matrix_calls"] = {"ms": ms_p, "GB/s": total / (ms_p * 1e-3) / 1e9, "launches": 2 * b.count}
-    out["batched_speedup_vs_per_matrix"] = ms_p / ms_b
+    out["per_matrix_ms"] = ms_p
+    out["per_matrix_GBps"] = total / (ms_p * 1e-3) / 1e9
+    out["per_matrix_launches"] = 2 * b.count
+    out["speedup_vs_per_matrix"] = ms_p / ms_b
     return out
 
 
