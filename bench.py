@@ -90,11 +90,11 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """Hash of the main kernel's source with comments and blank space removed, so a recorded
+def kernel_source_hash(files=("lb_merge.cuh", "lb_internal.cuh")) -> str:
+    """Hash of a kernel's source files with comments and blank space removed, so a recorded
     DRAM-traffic figure is used only while the code it was measured on is unchanged."""
     h = hashlib.sha256()
-    for f in ("lb_merge.cuh", "lb_internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2212_08964_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -104,14 +104,14 @@ def kernel_source_hash() -> str:
 
 
 def recorded_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, if the kernel source has
-    not changed since it was captured; else None."""
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if the kernel's source
+    files have not changed since it was captured; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(workload, {}).get(kernel)
-        if e and e.get("kernel_source_hash") == kernel_source_hash():
+        if e and e.get("kernel_source_hash") == kernel_source_hash(tuple(e["sources"])):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
