@@ -58,6 +58,8 @@ def _load():
             lib.oracle_spmv_t_f64.argtypes = [_i64, _i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
             lib.oracle_col_absdot.argtypes = [_i64, _i64, _i32p, _i32p, _f64p, _f64p, _f64p]
             lib.oracle_dvalues_f64.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
+            lib.oracle_spmm_f64.argtypes = [_i64, _i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
+            lib.oracle_spmm_absdot.argtypes = [_i64, _i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -77,6 +79,28 @@ def spmv(ro, ci, v, x, threads: int = 0) -> np.ndarray:
     y = np.empty(m, np.float64)
     _load().oracle_spmv_f64(m, ro, _c(ci, np.int32), _c(v, np.float64), _c(x, np.float64), y, threads)
     return y
+
+
+def spmm(ro, ci, v, B, threads: int = 0) -> np.ndarray:
+    """C = A B in FP64, B dense n x kc (row-major): SpMV with a loop over B's columns."""
+    ro = _c(ro, np.int32)
+    B = np.ascontiguousarray(B, np.float64)
+    m = ro.shape[0] - 1
+    kc = B.shape[1]
+    C = np.empty((m, kc), np.float64)
+    _load().oracle_spmm_f64(m, kc, ro, _c(ci, np.int32), _c(v, np.float64), B.reshape(-1), C.reshape(-1), threads)
+    return C
+
+
+def spmm_absdot(ro, ci, v, B, threads: int = 0) -> np.ndarray:
+    """sum_k |v_k||B[ci_k][j]| per entry of C."""
+    ro = _c(ro, np.int32)
+    B = np.ascontiguousarray(B, np.float64)
+    m = ro.shape[0] - 1
+    kc = B.shape[1]
+    S = np.empty((m, kc), np.float64)
+    _load().oracle_spmm_absdot(m, kc, ro, _c(ci, np.int32), _c(v, np.float64), B.reshape(-1), S.reshape(-1), threads)
+    return S
 
 
 def row_absdot(ro, ci, v, x, threads: int = 0) -> np.ndarray:

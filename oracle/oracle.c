@@ -28,6 +28,9 @@
  *     and COO views (Sec. "Implementing Sparse Data Structures").
  *   - Backward of L = 1/2 ||A x - t||^2: dx = A^T g with dx_j = sum over nonzeros of column
  *     j, in increasing k, of v_k g[row(k)]; dv_k = g[row(k)] * x[ci_k].
+ *   - SpMM C = A B with B dense n x kc, row-major (Sec. "Application Space", the SpMM
+ *     listing: SpMV with an extra loop over the columns of B):
+ *     C[i][j] = sum_{k = ro[i]}^{ro[i+1]-1} v_k * B[ci_k][j], summed sequentially in k.
  *
  * OpenMP only splits independent outputs (rows or columns); each output is summed in its
  * stated order, so results do not depend on the thread count.
@@ -62,6 +65,36 @@ void oracle_spmv_f64(int64_t m, const int32_t *ro, const int32_t *ci, const doub
         double s = 0.0;
         for (int64_t k = ro[i]; k < ro[i + 1]; ++k) s += v[k] * x[ci[k]];
         y[i] = s;
+    }
+}
+
+/* C = A B, B dense n x kc row-major; C m x kc row-major. */
+void oracle_spmm_f64(int64_t m, int64_t kc, const int32_t *ro, const int32_t *ci, const double *v,
+                     const double *B, double *C, int threads) {
+    int nt = oracle_threads(threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < kc; ++j) {
+            double s = 0.0;
+            for (int64_t k = ro[i]; k < ro[i + 1]; ++k) s += v[k] * B[(int64_t)ci[k] * kc + j];
+            C[i * kc + j] = s;
+        }
+    }
+}
+
+/* sum_k |v_k| |B[ci_k][j]| per entry of C: the scale of the per-entry error bound. */
+void oracle_spmm_absdot(int64_t m, int64_t kc, const int32_t *ro, const int32_t *ci, const double *v,
+                        const double *B, double *S, int threads) {
+    int nt = oracle_threads(threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < kc; ++j) {
+            double s = 0.0;
+            for (int64_t k = ro[i]; k < ro[i + 1]; ++k) s += fabs(v[k]) * fabs(B[(int64_t)ci[k] * kc + j]);
+            S[i * kc + j] = s;
+        }
     }
 }
 

@@ -306,3 +306,26 @@ def test_oracle_deterministic_across_threads(orc, name):
                lambda th: orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n, th),
                lambda th: orc.dvalues(a.row_offsets, a.col_idx, g, x, th)):
         assert np.array_equal(fn(1), fn(4))
+
+
+def test_spmm_pins(orc):
+    """SpMM against the dense product (numpy matmul of the dense A), against scipy's sparse
+    product, and column by column against SpMV; identity A returns B; a single column is SpMV."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(41)
+    a = synth.csr_from_row_lengths(rng, 90, rng.integers(0, 30, 70))
+    for kc in (1, 3, 4, 17):
+        B = rng.standard_normal((a.n, kc))
+        C = orc.spmm(a.row_offsets, a.col_idx, a.values, B)
+        A = sp.csr_matrix((a.values.astype(np.float64), a.col_idx, a.row_offsets), shape=(a.m, a.n))
+        np.testing.assert_allclose(C, A.toarray() @ B, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(C, (A @ B), rtol=1e-12, atol=1e-12)
+        for j in range(kc):
+            assert np.array_equal(C[:, j], orc.spmv(a.row_offsets, a.col_idx, a.values, B[:, j]))
+        S = orc.spmm_absdot(a.row_offsets, a.col_idx, a.values, B)
+        assert np.allclose(S, np.abs(A.toarray()) @ np.abs(B))
+        assert (np.abs(C) <= S + 1e-12).all()
+    eye = synth.from_dense(np.eye(6))
+    B = rng.standard_normal((6, 5))
+    assert np.array_equal(orc.spmm(eye.row_offsets, eye.col_idx, eye.values, B), B)
