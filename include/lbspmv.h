@@ -228,6 +228,19 @@ lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float
 lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
                            const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream);
 
+/*
+ * SpMM: C = A B with B dense (n x kc, row-major, FP32) and C (m x kc, row-major, FP32,
+ * overwritten), over the plan's merge-path partition: the dissertation's SpMV with a loop over
+ * the columns of B (Ch.4 Sec. "Application Space", the SpMM listing).  Each nonzero gathers a
+ * row of B as 16-byte vectors (scalar loads when kc % 4 != 0 or B, C are not 16-byte aligned);
+ * rows split across tiles are completed by a fixup of kc-wide carries in tile order, so C is
+ * deterministic.  Plans whose tiles exceed 2048 work items give LB_ERR_UNSUPPORTED.  The
+ * first call (and any call with more columns than before) allocates the plan's carry buffer
+ * (G * (kc + 1) * 4 bytes); later calls allocate nothing.
+ */
+lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, int kc,
+                          const float *B, float *C, cudaStream_t stream);
+
 void lb_plan_destroy(lb_plan *p);
 
 /*

@@ -151,6 +151,10 @@ struct lb_plan {
     int bucket_shift = 0;  // 0: one L2-sized bucket (CSR order, gathered through perm)
     int *bucket_pos = nullptr, *bucket_perm = nullptr;
     float *pv = nullptr;  // per call: values[k] * g[row(k)] in bucket order (nnz floats)
+    // SpMM carries, allocated on first use and grown with the number of columns.
+    int *mm_carry_row = nullptr;
+    float *mm_carry_val = nullptr;
+    long long mm_cols = 0;
 };
 
 struct lb_batched_plan {
@@ -181,6 +185,11 @@ static void release_transpose(lb_plan *p) {
 
 static void free_plan_arrays(lb_plan *p) {
     release_transpose(p);
+    if (p->mm_carry_row) cudaFree(p->mm_carry_row);
+    if (p->mm_carry_val) cudaFree(p->mm_carry_val);
+    p->mm_carry_row = nullptr;
+    p->mm_carry_val = nullptr;
+    p->mm_cols = 0;
     int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row};
     for (int *q : ints)
         if (q) cudaFree(q);
@@ -555,6 +564,31 @@ lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     return from_cuda(launch_dvalues(p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, nullptr, g, nullptr,
                                     x_gathered, dvalues, stream));
+}
+
+lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, int kc, const float *B,
+                          float *C, cudaStream_t stream) {
+    if (!p || !dtype_ok(vdt) || kc < 0) return LB_ERR_INVALID_ARG;
+    if (p->m == 0 || kc == 0) return LB_OK;
+    if (!C || (p->nnz > 0 && (!col_idx || !values || !B))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    const size_t c_bytes = static_cast<size_t>(p->m) * static_cast<size_t>(kc) * sizeof(float);
+    if (p->nnz == 0) return from_cuda(cudaMemsetAsync(C, 0, c_bytes, stream));
+    if (p->tile_items > 2048) return LB_ERR_UNSUPPORTED;  // SpMM stages tiles of up to 2048 items
+    if (kc > p->mm_cols) {
+        // Carries for G tiles of kc columns; allocated once per plan and column count growth.
+        if (p->mm_carry_row) cudaFree(p->mm_carry_row);
+        if (p->mm_carry_val) cudaFree(p->mm_carry_val);
+        p->mm_carry_row = nullptr;
+        p->mm_carry_val = nullptr;
+        p->mm_cols = 0;
+        cudaError_t e = dmalloc(&p->mm_carry_row, static_cast<size_t>(p->G));
+        if (e == cudaSuccess) e = dmalloc(&p->mm_carry_val, static_cast<size_t>(p->G) * static_cast<size_t>(kc));
+        if (e != cudaSuccess) return from_cuda(e);
+        p->mm_cols = kc;
+    }
+    return from_cuda(launch_spmm(vdt, p->G, p->m, kc, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx,
+                                 values, B, C, p->mm_carry_row, p->mm_carry_val, stream));
 }
 
 void lb_plan_destroy(lb_plan *p) {

@@ -214,6 +214,12 @@ cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *r
 cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, const int *mat_nz_base,
                                int *tile_mat, cudaStream_t stream);
 
+// SpMM C = A B (B dense n x kc row-major, C m x kc) over the forward partition (tiles of at
+// most 2048 items), then the fixup of the carries (carry_row[G], carry_val[G * kc]).
+cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, const int *tile_row, const int *tile_nz,
+                        const int *row_end, const int *ci, const void *values, const float *B, float *C,
+                        int *carry_row, float *carry_val, cudaStream_t st);
+
 cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
                             int *d_status, cudaStream_t stream);
 

@@ -219,23 +219,25 @@ __global__ void validate_offsets_kernel(int m, int nnz, const int *ro, int *stat
 
 // Column checks need row boundaries, which are only trustworthy when the offsets passed; the
 // kernel reads each row's range clamped to [0, nnz] so a broken offsets array cannot send it
-// out of bounds.
+// out of bounds.  A warp takes a row and its lanes stride over the row's nonzeros (coalesced),
+// so a row of half a million entries costs one warp a few thousand steps, not one thread.
 __global__ void validate_columns_kernel(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
                                         int *status) {
-    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < m;
-         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    int bits = 0;
+    for (long long r = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; r < m; r += warps) {
         long long b = ro[r], e = ro[r + 1];
         b = b < 0 ? 0 : (b > nnz ? nnz : b);
         e = e < b ? b : (e > nnz ? nnz : e);
-        int bits = 0, prev = -1;
-        for (long long k = b; k < e; ++k) {
+        for (long long k = b + lane; k < e; k += 32) {
             const int c = ci[k];
             if (c < 0 || c >= n) bits |= 8;
-            if (check_sorted && k > b && c <= prev) bits |= 16;
-            prev = c;
+            if (check_sorted && k > b && c <= ci[k - 1]) bits |= 16;
         }
-        if (bits) atomicOr(status, bits);
     }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if (lane == 0 && bits) atomicOr(status, bits);
 }
 
 cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted, int *d_status,
@@ -248,7 +250,10 @@ cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci,
     validate_offsets_kernel<<<blocks, 256, 0, stream>>>(m, nnz, ro, d_status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (m > 0 && nnz > 0) {
-        validate_columns_kernel<<<blocks, 256, 0, stream>>>(m, n, nnz, ro, ci, check_sorted, d_status);
+        long long wblocks = (static_cast<long long>(m) + 7) / 8;  // a warp per row
+        if (wblocks > current_sm_count() * 16) wblocks = current_sm_count() * 16;
+        validate_columns_kernel<<<static_cast<int>(wblocks), 256, 0, stream>>>(m, n, nnz, ro, ci, check_sorted,
+                                                                                d_status);
         e = cudaGetLastError();
     }
     return e;

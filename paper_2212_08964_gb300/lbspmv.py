@@ -106,6 +106,7 @@ def _declare(lib):
         "lb_spmv_planned_save": [_P, _P, _P, _I, _P, _P, _P, _P],
         "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _P],
         "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _P],
+        "lb_spmm_planned": [_P, _P, _P, _I, _I, _P, _P, _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -300,6 +301,22 @@ class Plan:
             _check(_lib.lb_spmv_planned_save(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(x), _ptr(y),
                                              _ptr(save_gathered), _stream(stream)), "lb_spmv_planned_save")
         return y
+
+    def spmm(self, col_idx, values, B, out=None, stream=None) -> torch.Tensor:
+        """C = A B (lb_spmm_planned): B float32 (n, kc) row-major, C float32 (m, kc)."""
+        _need(col_idx, torch.int32, "col_idx", self.nnz)
+        _need(values, None, "values", self.nnz)
+        if B.dim() != 2 or B.shape[0] != self.n:
+            raise ValueError(f"B must be ({self.n}, kc), got {tuple(B.shape)}")
+        _need(B, torch.float32, "B")
+        kc = B.shape[1]
+        C = torch.empty((self.m, kc), dtype=torch.float32, device=B.device) if out is None else out
+        if C.shape != (self.m, kc):
+            raise ValueError(f"out must be ({self.m}, {kc})")
+        _need(C, torch.float32, "out")
+        _check(_lib.lb_spmm_planned(self._h, _ptr(col_idx), _ptr(values), _vdt(values), kc, _ptr(B), _ptr(C),
+                                    _stream(stream)), "lb_spmm_planned")
+        return C
 
     # -- backward
     def build_transpose(self, col_idx, stream=None):
