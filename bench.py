@@ -483,6 +483,7 @@ def run_ours(args):
         mixed["stencil7_160_forward"] = run_stencil_precision(lb, torch, dev)
         result["mixed_precision"] = mixed
         result["batched"] = run_batched(lb, torch, dev)
+        result["spmm"] = run_spmm(lb, torch, dev, a, plan, ci, v, xd, y)
     if args.extras and rank == 0:
         result["extras"] = run_extras(lb, torch, dev)
 
@@ -548,6 +549,22 @@ def run_stencil_precision(lb, torch, dev):
             ms = _time(torch, lambda: plan.spmv(ci, v, x, out=y), 30)
             out[f"{sched}_{name}"] = {"ms": ms, "GBps": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9}
         out[f"{sched}_bf16_speedup_vs_f32"] = out[f"{sched}_f32"]["ms"] / out[f"{sched}_bf16"]["ms"]
+    return out
+
+
+def run_spmm(lb, torch, dev, a, plan, ci, v, xd, y):
+    """SpMM C = A B on the same matrix with B of 8 and 32 columns, against kc SpMV calls.
+    Bytes: nonzeros (value + index), row offsets, B and C once each."""
+    out = {}
+    spmv_ms = _time(torch, lambda: plan.spmv(ci, v, xd, out=y), 20)
+    for kc in (8, 32):
+        B = torch.rand(a.n, kc, device=dev) * 2 - 1
+        C = torch.empty(a.m, kc, device=dev)
+        ms = _time(torch, lambda: plan.spmm(ci, v, B, out=C), 10)
+        byts = a.nnz * 8 + 4 * (a.m + 1) + 4 * kc * (a.n + a.m)
+        out[f"kc{kc}"] = {"ms": ms, "GBps": byts / (ms * 1e-3) / 1e9, "GFLOPs": 2.0 * a.nnz * kc / (ms * 1e-3) / 1e9,
+                          "speedup_vs_kc_spmv_calls": kc * spmv_ms / ms}
+        del B, C
     return out
 
 

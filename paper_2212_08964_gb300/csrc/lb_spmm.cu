@@ -15,9 +15,10 @@
 //   2. threads are arranged as (column quad q, nonzero range g): thread (q, g) walks range g's
 //      nonzeros in order, accumulating B[col][4q .. 4q+3] * value per row, and writes rows that
 //      start and end inside its range straight to C;
-//   3. the first and last partial row of every range go through shared memory, and one thread
-//      per quad combines them in range order: completed rows to C, the open row to the tile's
-//      carry.  Rows without nonzeros in the tile that end there are written as zeros.
+//   3. the first and last partial row of every range go through shared memory; the range where
+//      a row first appears sums its partials forward through the ranges it spans and writes
+//      the row to C, or to the tile's carry when it is the row left open at the tile's end.
+//      Rows without nonzeros in the tile that end there are written as zeros.
 // Summation order is fixed (nonzero order within a tile, tile order in the fixup), so results
 // are deterministic.
 #include "lb_internal.cuh"
@@ -146,25 +147,49 @@ __global__ void __launch_bounds__(THREADS) spmm_kernel(int G, int m, int kc, int
         for (int qb = 0; qb < kq; qb += nq) {
             const int q = qb + q_loc;
             const bool active = q < kq;
+            if (active && g == 0) {  // the tile's carry is 0 unless the open row has nonzeros here
+                float *cv = carry_val + static_cast<long long>(tile) * kc + 4 * q;
+                if (4 * q < kc) cv[0] = 0.f;
+                if (4 * q + 1 < kc) cv[1] = 0.f;
+                if (4 * q + 2 < kc) cv[2] = 0.f;
+                if (4 * q + 3 < kc) cv[3] = 0.f;
+            }
             // Walk this range's nonzeros in order.
             int cur = -1, first_row = -1;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), first_acc = acc;
             if (active) {
-                for (int j = jb; j < je; ++j) {
-                    const int row = s_row[j];
-                    if (row != cur) {
-                        if (cur >= 0) {
-                            if (first_row < 0) {
-                                first_row = cur;
-                                first_acc = acc;
-                            } else {
-                                store_c4<VEC>(C, r0 + cur, kc, q, acc);  // started and ended in this range
-                            }
-                        }
-                        cur = row;
-                        acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                // Eight nonzeros at a time: their B rows are requested together before any is
+                // used, so each thread keeps eight gathers in flight.
+                constexpr int U = 8;
+                for (int j0 = jb; j0 < je; j0 += U) {
+                    float4 b[U];
+                    int rw[U];
+                    float vl[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = j0 + u;
+                        const bool in = j < je;
+                        rw[u] = in ? s_row[j] : -1;
+                        vl[u] = in ? s_val[j] : 0.f;
+                        b[u] = in ? load_b4<VEC>(B, s_col[j], kc, q) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    fma4(acc, s_val[j], load_b4<VEC>(B, s_col[j], kc, q));
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (rw[u] < 0) break;
+                        if (rw[u] != cur) {
+                            if (cur >= 0) {
+                                if (first_row < 0) {
+                                    first_row = cur;
+                                    first_acc = acc;
+                                } else {
+                                    store_c4<VEC>(C, r0 + cur, kc, q, acc);  // started and ended in this range
+                                }
+                            }
+                            cur = rw[u];
+                            acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        fma4(acc, vl[u], b[u]);
+                    }
                 }
             }
             if (first_row < 0) {  // the range holds at most one row
@@ -178,38 +203,38 @@ __global__ void __launch_bounds__(THREADS) spmm_kernel(int G, int m, int kc, int
                 p_acc[1][tid] = acc;
             }
             __syncthreads();
-            // One thread per quad joins the ranges' partial rows in order.
-            if (g == 0 && active) {
-                int row = -1;
-                float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int gg = 0; gg < ng; ++gg) {
-                    const int t = gg * nq + q_loc;
+            // Join the ranges' partial rows: the range where a row first appears in this tile
+            // (its head) sums that row's partials forward through the ranges it spans, then
+            // writes the row to C (it ends in the tile) or to the tile's carry (the open row).
+            if (active) {
 #pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        const int pr = p_row[w][t];
-                        if (pr < 0) continue;
-                        if (pr == row) {
-                            sum = add4(sum, p_acc[w][t]);
-                        } else {
-                            if (row >= 0) store_c4<VEC>(C, r0 + row, kc, q, sum);  // a later row follows
-                            row = pr;
-                            sum = p_acc[w][t];
+                for (int w = 0; w < 2; ++w) {
+                    const int R = p_row[w][tid];
+                    if (R < 0) continue;
+                    if (w == 0 && g > 0) {  // the first partial is a head unless range g-1 ends in R
+                        const int tp = (g - 1) * nq + q_loc;
+                        const int prev_last = p_row[1][tp] >= 0 ? p_row[1][tp] : p_row[0][tp];
+                        if (prev_last == R) continue;
+                    }
+                    float4 sum = p_acc[w][tid];
+                    if (w == 1 || p_row[1][tid] < 0) {  // R is this range's last row: it may go on
+                        for (int g2 = g + 1; g2 < ng; ++g2) {
+                            const int t2 = g2 * nq + q_loc;
+                            if (p_row[0][t2] != R) break;
+                            sum = add4(sum, p_acc[0][t2]);
+                            if (p_row[1][t2] >= 0) break;  // a new row starts inside range g2
                         }
                     }
+                    if (R < nr) {
+                        store_c4<VEC>(C, r0 + R, kc, q, sum);
+                    } else {
+                        float *cv = carry_val + static_cast<long long>(tile) * kc + 4 * q;
+                        if (4 * q < kc) cv[0] = sum.x;
+                        if (4 * q + 1 < kc) cv[1] = sum.y;
+                        if (4 * q + 2 < kc) cv[2] = sum.z;
+                        if (4 * q + 3 < kc) cv[3] = sum.w;
+                    }
                 }
-                // The tile's last row with nonzeros: complete if it ends inside the tile, else
-                // the open row r1 and the tile's carry.
-                if (row >= 0 && row < nr) {
-                    store_c4<VEC>(C, r0 + row, kc, q, sum);
-                    sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                } else if (row < 0) {
-                    sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                float *cv = carry_val + static_cast<long long>(tile) * kc + 4 * q;
-                if (4 * q < kc) cv[0] = sum.x;
-                if (4 * q + 1 < kc) cv[1] = sum.y;
-                if (4 * q + 2 < kc) cv[2] = sum.z;
-                if (4 * q + 3 < kc) cv[3] = sum.w;
             }
             __syncthreads();
         }
