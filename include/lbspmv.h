@@ -308,6 +308,17 @@ lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *
                           lb_tune_result *results, int capacity, int *count_out, cudaStream_t stream);
 
 /*
+ * COO input (the framework's COO view of a sparse matrix, Ch.4 Sec. "Implementing Sparse Data
+ * Structures"): for a COO matrix sorted by row (row_idx[nnz], device), write its CSR row
+ * offsets row_offsets[m + 1] (device): row_offsets[r] = #{k : row_idx[k] < r}.  Then
+ * (row_offsets, col_idx, values) is the same matrix in CSR form and every call above applies.
+ * A check writes a bit mask to the device int *d_status: 1 a row index outside [0, m), 2 the
+ * rows decrease somewhere (0 = valid; the offsets mean nothing otherwise).  No allocation.
+ */
+lb_status lb_coo_row_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
+                             cudaStream_t stream);
+
+/*
  * Check a CSR matrix on the device and write a bit mask to the device int *d_status
  * (0 = valid): 1 row_offsets[0] != 0; 2 row_offsets decreasing somewhere; 4
  * row_offsets[m] != nnz; 8 a column index outside [0, n); 16 (only with check_sorted)

@@ -751,6 +751,13 @@ void lb_batched_plan_destroy(lb_batched_plan *p) {
     delete p;
 }
 
+lb_status lb_coo_row_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
+                             cudaStream_t stream) {
+    if (m < 0 || nnz < 0 || (m == 0 && nnz != 0) || !row_offsets || !d_status || (nnz > 0 && !row_idx))
+        return LB_ERR_INVALID_ARG;
+    return from_cuda(launch_coo_offsets(m, nnz, row_idx, row_offsets, d_status, stream));
+}
+
 lb_status lb_validate_csr(int m, int n, int nnz, const int *row_offsets, const int *col_idx, int check_sorted,
                           int *d_status, cudaStream_t stream) {
     if (!sizes_ok(m, n, nnz) || !d_status || !row_offsets || (nnz > 0 && !col_idx)) return LB_ERR_INVALID_ARG;

@@ -220,6 +220,11 @@ cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, cons
                         const int *row_end, const int *ci, const void *values, const float *B, float *C,
                         int *carry_row, float *carry_val, cudaStream_t st);
 
+// Row offsets (m + 1) of a row-sorted COO matrix; *d_status gets 1 (row out of range) | 2
+// (rows decrease) | 0.
+cudaError_t launch_coo_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
+                               cudaStream_t stream);
+
 cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
                             int *d_status, cudaStream_t stream);
 

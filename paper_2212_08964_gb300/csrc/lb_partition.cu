@@ -240,6 +240,54 @@ __global__ void validate_columns_kernel(int m, int n, int nnz, const int *ro, co
     if (lane == 0 && bits) atomicOr(status, bits);
 }
 
+// ------------------------------------------------------------------------------------------
+// COO input (the framework's COO view, Ch.4 Sec. "Implementing Sparse Data Structures"): row
+// offsets of a row-sorted COO matrix, ro[r] = #{k : row_idx[k] < r} (a lower bound per row),
+// so that (ro, col_idx, values) is the same matrix in CSR and every schedule applies
+// unchanged.  A check pass ORs 1 into *status for a row index outside [0, m) and 2 for a
+// decrease; the offsets are only meaningful when it stays 0.
+__global__ void coo_check_kernel(int m, int nnz, const int *__restrict__ row_idx, int *status) {
+    int bits = 0;
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < nnz;
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int r = __ldg(row_idx + k);
+        if (r < 0 || r >= m) bits |= 1;
+        if (k > 0 && r < __ldg(row_idx + k - 1)) bits |= 2;
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
+}
+
+__global__ void coo_offsets_kernel(int m, int nnz, const int *__restrict__ row_idx, int *__restrict__ ro) {
+    for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r <= m;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        long long lo = 0, hi = nnz;  // first k with row_idx[k] >= r
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (__ldg(row_idx + mid) < r)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        ro[r] = static_cast<int>(lo);
+    }
+}
+
+cudaError_t launch_coo_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
+                               cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    const long long cap = static_cast<long long>(current_sm_count()) * 16;
+    if (nnz > 0) {
+        long long b = (static_cast<long long>(nnz) + 255) / 256;
+        coo_check_kernel<<<static_cast<int>(b < cap ? b : cap), 256, 0, stream>>>(m, nnz, row_idx, d_status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    long long b = (static_cast<long long>(m) + 1 + 255) / 256;
+    coo_offsets_kernel<<<static_cast<int>(b < cap ? b : cap), 256, 0, stream>>>(m, nnz, row_idx, row_offsets);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted, int *d_status,
                             cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), stream);

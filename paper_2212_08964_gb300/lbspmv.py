@@ -33,6 +33,7 @@ __all__ = [
     "SpMV",
     "spmv_autograd",
     "validate_csr",
+    "coo_row_offsets",
     "device_error",
     "set_profile_events",
     "SCHEDULES",
@@ -107,6 +108,7 @@ def _declare(lib):
         "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _P],
         "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _P],
         "lb_spmm_planned": [_P, _P, _P, _I, _I, _P, _P, _P],
+        "lb_coo_row_offsets": [_I, _I, _P, _P, _P, _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -488,6 +490,18 @@ class SpMV(torch.autograd.Function):
 def spmv_autograd(plan: Plan, col_idx, values, x):
     """Differentiable y = A x (see ``SpMV``)."""
     return SpMV.apply(values, x, plan, col_idx)
+
+
+def coo_row_offsets(row_idx, m: int, stream=None):
+    """CSR row offsets (int32 device tensor of m + 1) of a row-sorted COO matrix, and the check
+    mask (1: row out of range, 2: rows decrease; 0: valid); reading the mask synchronizes."""
+    lib = ensure_loaded()
+    _need(row_idx, torch.int32, "row_idx")
+    ro = torch.empty(m + 1, dtype=torch.int32, device=row_idx.device)
+    status = torch.zeros(1, dtype=torch.int32, device=row_idx.device)
+    _check(lib.lb_coo_row_offsets(m, row_idx.numel(), _ptr(row_idx) if row_idx.numel() else None, _ptr(ro),
+                                  _ptr(status), _stream(stream)), "lb_coo_row_offsets")
+    return ro, int(status.item())
 
 
 def validate_csr(row_offsets, col_idx, n: int, check_sorted: bool = True, stream=None) -> int:

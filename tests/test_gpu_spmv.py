@@ -271,3 +271,37 @@ def test_full_size_powerlaw_8m_half(lb, orc, dtype):
     r16, s16 = _ref(orc, a, x, rounded(a.values, dtype))
     check_bound(y, r16, s16, TOL32)
     print(f"powerlaw_8m {dtype}: vs FP32 values max {mx:.3e} median {med:.3e}")
+
+
+@pytest.mark.parametrize("name", ["powerlaw_4k", "stencil", "empty_rows"])
+def test_coo_input(lb, orc, name):
+    """COO (row-sorted) to CSR offsets bit-exact against counting; the COO matrix then runs
+    through the plain entry point; unsorted and out-of-range rows are reported."""
+    if name == "powerlaw_4k":
+        a = workload("powerlaw_4k")
+    elif name == "stencil":
+        a = synth.stencil7_csr(9, seed=3)
+    else:
+        rng = np.random.default_rng(3)
+        lengths = rng.integers(0, 4, 5000)
+        lengths[:100] = 0
+        lengths[-300:] = 0
+        a = synth.csr_from_row_lengths(rng, 700, lengths)
+    rows = np.repeat(np.arange(a.m, dtype=np.int32), a.row_lengths())
+    ro, status = lb.coo_row_offsets(dev(rows), a.m)
+    assert status == 0
+    counted = np.array([np.count_nonzero(rows < r) for r in range(a.m + 1)], dtype=np.int32)
+    assert np.array_equal(ro.cpu().numpy(), counted)
+    assert np.array_equal(counted, a.row_offsets)
+    x = vec(a.n, 61)
+    y = lb.spmv(ro, dev(a.col_idx), dev(a.values), dev(x), n=a.n)
+    torch.cuda.synchronize()
+    check_bound(y.cpu().numpy(), orc.spmv(a.row_offsets, a.col_idx, a.values, x),
+                orc.row_absdot(a.row_offsets, a.col_idx, a.values, x), TOL32)
+    if rows.size > 2:
+        bad = rows.copy()
+        bad[1], bad[-1] = bad[-1], bad[1]
+        assert lb.coo_row_offsets(dev(bad), a.m)[1] & 2
+        bad = rows.copy()
+        bad[-1] = a.m
+        assert lb.coo_row_offsets(dev(bad), a.m)[1] & 1
