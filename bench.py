@@ -381,11 +381,23 @@ def run_ours(args):
         "csr_backward_kernel (dvalues, v*g[row] into CSC buckets)": (mean_ms(evd_b, evt_b), csr_b),
         "merge_spmv_kernel<gather-sum> (dx = A^T g)": (mean_ms(evt_b, evt_a), gs_b),
     }
+    # 32-byte sector requests from the SMs to L2 per launch: one per random gather plus the
+    # streamed bytes (algorithmic, everything except the gathered vector) in sectors.
+    sectors = {
+        "merge_spmv_kernel<plain> (y = A x, saving x[col])": a.nnz + (fwd_b + 4 * a.nnz - 4 * a.n) / 32,
+        "csr_backward_kernel (dvalues, v*g[row] into CSC buckets)": csr_b / 32,
+        "merge_spmv_kernel<gather-sum> (dx = A^T g)": a.nnz + (gs_b - 4 * a.nnz) / 32,
+    }
     assert lb.device_error() == 0
 
     peak, peak_kind = measured_hbm_peak()
+    calib = lb.calibrate() if rank == 0 else None
     kernels = {k: {"avg_launch_ms": t, "algorithmic_bytes_per_launch": b, "achieved_GBps": b / (t * 1e-3) / 1e9,
-                   "frac": b / (t * 1e-3) / 1e9 / peak} for k, (t, b) in kern.items()}
+                   "frac": b / (t * 1e-3) / 1e9 / peak, "sector_requests_per_launch": sectors[k],
+                   "sector_requests_per_s": sectors[k] / (t * 1e-3)} for k, (t, b) in kern.items()}
+    if calib:
+        for k in kernels:
+            kernels[k]["frac_of_measured_gather_rate"] = kernels[k]["sector_requests_per_s"] / calib["gathers_per_s"]
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_b = kern[dom]
     achieved = dom_b / (dom_ms * 1e-3) / 1e9
@@ -425,6 +437,12 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": dom_b, "avg_launch_ms": dom_ms,
         },
         "kernels": kernels,
+        "calibration": calib,
+        "roofline_requests": None if not calib else {
+            "bound": "SM-to-L2 sector requests (one per random gather)", "kernel": dom,
+            "achieved": sectors[dom] / (dom_ms * 1e-3), "peak": calib["gathers_per_s"], "unit": "requests/s",
+            "frac": sectors[dom] / (dom_ms * 1e-3) / calib["gathers_per_s"],
+            "peak_kind": "measured by lb_calibrate in this run (random 4-byte gathers from a 16 MB vector)"},
         "gpu_launches": launches_per_step * K,
         "clocks": clocks.summary(),
     }

@@ -308,6 +308,22 @@ lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *
                           lb_tune_result *results, int capacity, int *count_out, cudaStream_t stream);
 
 /*
+ * Measured ceilings of the current GPU for the roofline of these kernels (no counterpart in
+ * the dissertation): the rate of random 4-byte gathers from an L2-resident 16 MB vector
+ * (every gather is its own 32-byte sector request from an SM to L2, the limit of SpMV with
+ * scattered columns), and streaming read and copy bandwidth over 1 GiB buffers.  Each is the
+ * best of three timed runs after a warm-up.  Allocates about 2 GiB temporarily and
+ * synchronizes `stream`.
+ */
+typedef struct {
+    double gathers_per_s; /* random 4-byte gathers (sector requests) per second */
+    double read_GBps;     /* streaming read, 1e9 bytes per second */
+    double copy_GBps;     /* streaming copy, bytes read + written, 1e9 bytes per second */
+} lb_calibration;
+
+lb_status lb_calibrate(lb_calibration *out, cudaStream_t stream);
+
+/*
  * COO input (the framework's COO view of a sparse matrix, Ch.4 Sec. "Implementing Sparse Data
  * Structures"): for a COO matrix sorted by row (row_idx[nnz], device), write its CSR row
  * offsets row_offsets[m + 1] (device): row_offsets[r] = #{k : row_idx[k] < r}.  Then

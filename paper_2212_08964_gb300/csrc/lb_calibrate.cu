@@ -1,0 +1,121 @@
+// lb_calibrate.cu -- measured ceilings of this GPU for the roofline of the SpMV kernels.
+//
+// Two numbers bound a load-balanced SpMV on GB300.  Streaming the matrix is bound by HBM
+// bandwidth.  Gathering x, where every nonzero gathers a 4-byte entry from an arbitrary
+// column, is bound by how many 32-byte sector requests an SM's L1 can send to L2 per unit
+// of time: each random gather is its own request, whatever the DRAM traffic.  lb_calibrate
+// measures both with small kernels of its own:
+//   - random 4-byte gathers from an L2-resident 16 MB vector, eight independent gathers per
+//     thread in flight, indices from a counter-based hash (no index stream);
+//   - a streaming read (16-byte loads, summed) and a copy over 1 GiB buffers.
+// The kernels exist for this measurement only; the SpMV path does not use them.
+#include <cstdint>
+
+#include "lb_internal.cuh"
+
+namespace {
+
+// SplitMix64 finaliser (Steele, Lea, Flood, "Fast splittable pseudorandom number generators").
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(256) gather_probe_kernel(const float *__restrict__ x, unsigned mask, long long n,
+                                                           float *out) {
+    float acc = 0.f;
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x * 8;
+    for (long long base = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 8; base < n;
+         base += stride) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(x + (static_cast<unsigned>(mix64(base + u)) & mask));
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    if (acc == 1.2345678e30f) out[0] = acc;  // keeps the loads; never true for the data used
+}
+
+__global__ void __launch_bounds__(256) read_probe_kernel(const float4 *__restrict__ a, long long n4, float *out) {
+    float acc = 0.f;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float4 v = __ldcs(a + i);
+        acc += v.x + v.y + v.z + v.w;
+    }
+    if (acc == 1.2345678e30f) out[0] = acc;
+}
+
+__global__ void __launch_bounds__(256) copy_probe_kernel(const float4 *__restrict__ a, float4 *__restrict__ b,
+                                                         long long n4) {
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        __stcs(b + i, __ldcs(a + i));
+}
+
+template <typename F>
+cudaError_t best_of(int reps, cudaStream_t st, F launch, float *best_ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) {
+            launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0 && ms < best) best = ms;  // the first run warms up
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *best_ms = best;
+    return e;
+}
+
+}  // namespace
+
+extern "C" lb_status lb_calibrate(lb_calibration *out, cudaStream_t stream) {
+    if (!out) return LB_ERR_INVALID_ARG;
+    const long long kBuf = 1ll << 28;       // 256M floats = 1 GiB per buffer
+    const long long kVec = 1ll << 22;       // 4M floats = 16 MB gathered vector
+    const long long kGathers = 1ll << 26;   // 64M gathers
+    float *a = nullptr, *b = nullptr, *x = nullptr, *sink = nullptr;
+    cudaError_t e = cudaMalloc(&a, kBuf * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b, kBuf * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&x, kVec * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, kBuf * sizeof(float), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, kVec * sizeof(float), stream);
+    const int sms = lb::current_sm_count();
+    float ms_g = 0.f, ms_r = 0.f, ms_c = 0.f;
+    if (e == cudaSuccess)
+        e = best_of(4, stream, [&]() {
+            gather_probe_kernel<<<sms * 8, 256, 0, stream>>>(x, static_cast<unsigned>(kVec - 1), kGathers, sink);
+        }, &ms_g);
+    if (e == cudaSuccess)
+        e = best_of(4, stream, [&]() {
+            read_probe_kernel<<<sms * 8, 256, 0, stream>>>(reinterpret_cast<const float4 *>(a), kBuf / 4, sink);
+        }, &ms_r);
+    if (e == cudaSuccess)
+        e = best_of(4, stream, [&]() {
+            copy_probe_kernel<<<sms * 8, 256, 0, stream>>>(reinterpret_cast<const float4 *>(a),
+                                                            reinterpret_cast<float4 *>(b), kBuf / 8);
+        }, &ms_c);
+    if (e == cudaSuccess) {
+        out->gathers_per_s = static_cast<double>(kGathers) / (ms_g * 1e-3);
+        out->read_GBps = static_cast<double>(kBuf) * sizeof(float) / (ms_r * 1e-3) / 1e9;
+        out->copy_GBps = 2.0 * static_cast<double>(kBuf / 2) * sizeof(float) / (ms_c * 1e-3) / 1e9;
+    }
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (x) cudaFree(x);
+    if (sink) cudaFree(sink);
+    return e == cudaSuccess ? LB_OK : (e == cudaErrorMemoryAllocation ? LB_ERR_NO_MEMORY : LB_ERR_CUDA);
+}

@@ -106,9 +106,9 @@ struct StageHdr {
 
 // Shared-memory mbarriers of one CTA.
 struct Bars {
-    uint64_t full[3];    // stage s holds tile data (producer arm + TMA bytes)
-    uint64_t gdone[3];   // gather warps finished reading stage s (one arrival per gather warp)
-    uint64_t sdone[3];   // scan warps finished with stage s (one arrival)
+    uint64_t full[4];    // stage s holds tile data (producer arm + TMA bytes)
+    uint64_t gdone[4];   // gather warps finished reading stage s (one arrival per gather warp)
+    uint64_t sdone[4];   // scan warps finished with stage s (one arrival)
     uint64_t pready[2];  // product buffer b filled (one arrival per gather warp)
     uint64_t pfree[2];   // product buffer b consumed (one arrival)
 };

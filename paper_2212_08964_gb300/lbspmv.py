@@ -34,6 +34,7 @@ __all__ = [
     "spmv_autograd",
     "validate_csr",
     "coo_row_offsets",
+    "calibrate",
     "device_error",
     "set_profile_events",
     "SCHEDULES",
@@ -76,6 +77,12 @@ class _Tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("items_per_thread", ctypes.c_int), ("group_size", ctypes.c_int)]
 
 
+class Calibration(ctypes.Structure):
+    """lb_calibration: measured gather rate and streaming bandwidths of the current GPU."""
+
+    _fields_ = [("gathers_per_s", ctypes.c_double), ("read_GBps", ctypes.c_double), ("copy_GBps", ctypes.c_double)]
+
+
 class TuneResult(ctypes.Structure):
     """lb_tune_result: a candidate's schedule, resolved launch shape and mean milliseconds."""
 
@@ -109,6 +116,7 @@ def _declare(lib):
         "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _P],
         "lb_spmm_planned": [_P, _P, _P, _I, _I, _P, _P, _P],
         "lb_coo_row_offsets": [_I, _I, _P, _P, _P, _P],
+        "lb_calibrate": [ctypes.POINTER(Calibration), _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -502,6 +510,15 @@ def coo_row_offsets(row_idx, m: int, stream=None):
     _check(lib.lb_coo_row_offsets(m, row_idx.numel(), _ptr(row_idx) if row_idx.numel() else None, _ptr(ro),
                                   _ptr(status), _stream(stream)), "lb_coo_row_offsets")
     return ro, int(status.item())
+
+
+def calibrate(stream=None) -> dict:
+    """Measured ceilings of the current GPU (lb_calibrate): gathers per second and streaming
+    read / copy GB/s."""
+    lib = ensure_loaded()
+    c = Calibration()
+    _check(lib.lb_calibrate(ctypes.byref(c), _stream(stream)), "lb_calibrate")
+    return {"gathers_per_s": c.gathers_per_s, "read_GBps": c.read_GBps, "copy_GBps": c.copy_GBps}
 
 
 def validate_csr(row_offsets, col_idx, n: int, check_sorted: bool = True, stream=None) -> int:

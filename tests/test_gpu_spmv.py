@@ -305,3 +305,11 @@ def test_coo_input(lb, orc, name):
         bad = rows.copy()
         bad[-1] = a.m
         assert lb.coo_row_offsets(dev(bad), a.m)[1] & 1
+
+
+def test_calibrate(lb):
+    """The measured ceilings are positive and in the range this part can reach."""
+    c = lb.calibrate()
+    assert 1e10 < c["gathers_per_s"] < 5e12
+    assert 100 < c["read_GBps"] < 20000
+    assert 100 < c["copy_GBps"] < 20000
