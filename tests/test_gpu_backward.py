@@ -267,3 +267,36 @@ def test_bucketed_value_permutation(lb, orc, monkeypatch):
         co, ri, perm = plan.transpose()
         oco, ori, operm = orc.transpose(a.row_offsets, a.col_idx, a.n)
         assert np.array_equal(perm, operm) and np.array_equal(ri, ori)
+
+
+def test_training_step_in_a_cuda_graph(lb, orc):
+    """Forward saving its gathers plus the two-pass backward, captured once in a CUDA graph and
+    replayed: the same bits as eager calls (no allocation or synchronization inside)."""
+    a = workload("lognormal_1m", 0.1)
+    plan, ci, v = _plan_with_t(lb, a)
+    x, g = dev(vec(a.n, 221)), dev(vec(a.m, 222))
+    y, dx = torch.empty(a.m, device="cuda"), torch.empty(a.n, device="cuda")
+    dv, xg = torch.empty(a.nnz, device="cuda"), torch.empty(a.nnz, device="cuda")
+
+    def step():
+        plan.spmv(ci, v, x, out=y, save_gathered=xg)
+        plan.backward(v, g, xg, dx=dx, dvalues=dv)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()  # first calls outside the capture (kernel attributes, occupancy queries)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    ref = (y.clone(), dx.clone(), dv.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for t in (y, dx, dv):
+        t.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref[0]) and torch.equal(dx, ref[1]) and torch.equal(dv, ref[2])
+    check_bound(dx.cpu().numpy(), orc.spmv_t(a.row_offsets, a.col_idx, a.values, vec(a.m, 222), a.n),
+                orc.col_absdot(a.row_offsets, a.col_idx, a.values, vec(a.m, 222), a.n), TOL32, "columns")
