@@ -60,6 +60,8 @@ def _load():
             lib.oracle_dvalues_f64.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
             lib.oracle_spmm_f64.argtypes = [_i64, _i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
             lib.oracle_spmm_absdot.argtypes = [_i64, _i64, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int]
+            lib.oracle_sssp_f64.argtypes = [_i64, _i32p, _i32p, ctypes.c_void_p, _i64, _f64p]
+            lib.oracle_sssp_f64.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -101,6 +103,22 @@ def spmm_absdot(ro, ci, v, B, threads: int = 0) -> np.ndarray:
     S = np.empty((m, kc), np.float64)
     _load().oracle_spmm_absdot(m, kc, ro, _c(ci, np.int32), _c(v, np.float64), B.reshape(-1), S.reshape(-1), threads)
     return S
+
+
+def sssp(ro, ci, w, source: int) -> np.ndarray:
+    """Shortest-path distances from `source` over a CSR graph (Dijkstra, FP64); w None: unit
+    weights (BFS levels).  +inf for unreachable vertices."""
+    ro = _c(ro, np.int32)
+    n = ro.shape[0] - 1
+    dist = np.empty(n, np.float64)
+    wp = None
+    if w is not None:
+        w = _c(w, np.float64)
+        wp = w.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().oracle_sssp_f64(n, ro, _c(ci, np.int32), wp, int(source), dist)
+    if rc != 0:
+        raise ValueError(f"oracle_sssp_f64 failed ({rc})")
+    return dist
 
 
 def row_absdot(ro, ci, v, x, threads: int = 0) -> np.ndarray:

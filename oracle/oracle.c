@@ -31,6 +31,10 @@
  *   - SpMM C = A B with B dense n x kc, row-major (Sec. "Application Space", the SpMM
  *     listing: SpMV with an extra loop over the columns of B):
  *     C[i][j] = sum_{k = ro[i]}^{ro[i+1]-1} v_k * B[ci_k][j], summed sequentially in k.
+ *   - Single-source shortest paths over a CSR graph with non-negative edge weights (Sec.
+ *     "Application Space", the SSSP listing): dist[v] = min over paths from the source of the
+ *     sum of edge weights, +inf if unreachable.  The oracle is Dijkstra's algorithm with a
+ *     binary heap (any correct method gives the same minimum); sums in FP64.
  *
  * OpenMP only splits independent outputs (rows or columns); each output is summed in its
  * stated order, so results do not depend on the thread count.
@@ -201,4 +205,68 @@ void oracle_dvalues_f64(int64_t m, const int32_t *ro, const int32_t *ci, const d
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
     for (int64_t r = 0; r < m; ++r)
         for (int64_t k = ro[r]; k < ro[r + 1]; ++k) dv[k] = g[r] * x[ci[k]];
+}
+
+/* ----------------------------------------------------------------------------------------
+ * Single-source shortest paths: Dijkstra with a binary heap of (distance, vertex) pairs and
+ * lazy deletion.  Edges u -> ci[k] for k in [ro[u], ro[u+1]) with weight w[k] >= 0 (w == NULL:
+ * every weight 1, so dist is the BFS level).  dist[v] = INFINITY when v is unreachable. */
+typedef struct {
+    double d;
+    int64_t v;
+} heap_item;
+
+static void heap_push(heap_item *h, int64_t *size, heap_item it) {
+    int64_t i = (*size)++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p].d <= it.d) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = it;
+}
+
+static heap_item heap_pop(heap_item *h, int64_t *size) {
+    heap_item top = h[0];
+    heap_item last = h[--(*size)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *size) break;
+        if (c + 1 < *size && h[c + 1].d < h[c].d) ++c;
+        if (last.d <= h[c].d) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*size > 0) h[i] = last;
+    return top;
+}
+
+int oracle_sssp_f64(int64_t n, const int32_t *ro, const int32_t *ci, const double *w, int64_t source,
+                    double *dist) {
+    for (int64_t v = 0; v < n; ++v) dist[v] = INFINITY;
+    if (source < 0 || source >= n) return -1;
+    int64_t cap = (int64_t)ro[n] + 1;
+    heap_item *h = (heap_item *)malloc((size_t)cap * sizeof(heap_item));
+    if (!h) return -2;
+    int64_t size = 0;
+    dist[source] = 0.0;
+    heap_item s0 = {0.0, source};
+    heap_push(h, &size, s0);
+    while (size > 0) {
+        heap_item it = heap_pop(h, &size);
+        if (it.d > dist[it.v]) continue; /* stale entry */
+        for (int64_t k = ro[it.v]; k < ro[it.v + 1]; ++k) {
+            double nd = it.d + (w ? w[k] : 1.0);
+            int64_t u = ci[k];
+            if (nd < dist[u]) {
+                dist[u] = nd;
+                heap_item e = {nd, u};
+                heap_push(h, &size, e); /* at most one push per edge: fits cap */
+            }
+        }
+    }
+    free(h);
+    return 0;
 }

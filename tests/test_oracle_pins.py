@@ -329,3 +329,29 @@ def test_spmm_pins(orc):
     eye = synth.from_dense(np.eye(6))
     B = rng.standard_normal((6, 5))
     assert np.array_equal(orc.spmm(eye.row_offsets, eye.col_idx, eye.values, B), B)
+
+
+def test_sssp_pins(orc):
+    """Dijkstra against scipy's shortest paths (weighted and unweighted), and a hand-worked
+    graph: 0 -> 1 (4), 0 -> 2 (1), 2 -> 1 (2), 1 -> 3 (1), 3 unreachable from 4."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+
+    ro = np.array([0, 2, 3, 4, 4, 4], np.int32)
+    ci = np.array([1, 2, 3, 1], np.int32)
+    w = np.array([4.0, 1.0, 1.0, 2.0])
+    d = orc.sssp(ro, ci, w, 0)
+    assert d[:4].tolist() == [0.0, 3.0, 1.0, 4.0] and np.isinf(d[4])
+    assert orc.sssp(ro, ci, None, 0)[:4].tolist() == [0.0, 1.0, 1.0, 2.0]
+    rng = np.random.default_rng(77)
+    a = synth.csr_from_row_lengths(rng, 400, rng.integers(0, 6, 400))
+    wts = rng.uniform(0.5, 3.0, a.nnz)
+    G = sp.csr_matrix((wts, a.col_idx, a.row_offsets), shape=(400, 400))
+    for src in (0, 7, 399):
+        ref = shortest_path(G, method="D", directed=True, indices=src)
+        got = orc.sssp(a.row_offsets, a.col_idx, wts, src)
+        assert np.array_equal(np.isinf(ref), np.isinf(got))
+        fin = np.isfinite(ref)
+        np.testing.assert_allclose(got[fin], ref[fin], rtol=1e-12)
+        ref_u = shortest_path(G, method="D", directed=True, unweighted=True, indices=src)
+        assert np.array_equal(orc.sssp(a.row_offsets, a.col_idx, None, src), ref_u)
