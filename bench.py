@@ -502,6 +502,7 @@ def run_ours(args):
         result["mixed_precision"] = mixed
         result["batched"] = run_batched(lb, torch, dev)
         result["spmm"] = run_spmm(lb, torch, dev, a, plan, ci, v, xd, y)
+        result["sssp"] = run_sssp(lb, torch, dev, a, ro, ci)
     if args.extras and rank == 0:
         result["extras"] = run_extras(lb, torch, dev)
 
@@ -583,6 +584,26 @@ def run_spmm(lb, torch, dev, a, plan, ci, v, xd, y):
         out[f"kc{kc}"] = {"ms": ms, "GBps": byts / (ms * 1e-3) / 1e9, "GFLOPs": 2.0 * a.nnz * kc / (ms * 1e-3) / 1e9,
                           "speedup_vs_kc_spmv_calls": kc * spmv_ms / ms}
         del B, C
+    return out
+
+
+def run_sssp(lb, torch, dev, a, ro, ci):
+    """SSSP and BFS from vertex 0 over the same matrix read as a directed graph (integer
+    weights 1..99, then unit weights), wall time per run including the per-iteration host
+    synchronizations; edges/s counts the graph's edges."""
+    w = torch.randint(1, 100, (a.nnz,), device=dev, generator=torch.Generator(device=dev).manual_seed(7)).float()
+    out = {}
+    for name, wt in (("sssp", w), ("bfs", None)):
+        lb.sssp(ro, ci, wt, 0)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            dist, iters = lb.sssp(ro, ci, wt, 0)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        out[name] = {"ms": ms, "iterations": iters, "edges_per_s": a.nnz / (ms * 1e-3),
+                     "reachable": int(torch.isfinite(dist).sum().item())}
     return out
 
 

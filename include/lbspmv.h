@@ -308,6 +308,22 @@ lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *
                           lb_tune_result *results, int capacity, int *count_out, cudaStream_t stream);
 
 /*
+ * Single-source shortest paths over a directed graph in CSR form (vertex u's out-edges are
+ * u -> col_idx[k], k in [row_offsets[u], row_offsets[u+1]), n vertices), expressed on the
+ * load-balancing schedules as in Ch.4 Sec. "Application Space" (the SSSP listing): the
+ * frontier's edges are the atoms, split evenly over the threads; relaxing an edge lowers the
+ * neighbour's distance with an atomic minimum and puts the neighbour on the next frontier when
+ * it dropped; the host iterates until the frontier is empty.  weights: nnz non-negative FP32
+ * values, or NULL for unit weights (dist = BFS level).  dist (n floats, device) receives the
+ * distances (+inf when unreachable); *iterations (host) the number of frontier iterations.
+ * FP32 sums: each distance is the minimum over paths of the FP32 sum along the path.
+ * Allocates its workspace (about 16 bytes per vertex) and synchronizes `stream` once or twice
+ * per iteration.  Negative weights are not supported (the iteration count is capped at n + 1).
+ */
+lb_status lb_sssp(int n, int nnz, const int *row_offsets, const int *col_idx, const float *weights,
+                  int source, float *dist, int *iterations, cudaStream_t stream);
+
+/*
  * Measured ceilings of the current GPU for the roofline of these kernels (no counterpart in
  * the dissertation): the rate of random 4-byte gathers from an L2-resident 16 MB vector
  * (every gather is its own 32-byte sector request from an SM to L2, the limit of SpMV with

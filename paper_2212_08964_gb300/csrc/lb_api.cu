@@ -751,6 +751,13 @@ void lb_batched_plan_destroy(lb_batched_plan *p) {
     delete p;
 }
 
+lb_status lb_sssp(int n, int nnz, const int *row_offsets, const int *col_idx, const float *weights, int source,
+                  float *dist, int *iterations, cudaStream_t stream) {
+    if (n <= 0 || nnz < 0 || source < 0 || source >= n || !row_offsets || !dist || !iterations) return LB_ERR_INVALID_ARG;
+    if (nnz > 0 && !col_idx) return LB_ERR_INVALID_ARG;
+    return from_cuda(run_sssp(n, nnz, row_offsets, col_idx, weights, source, dist, iterations, stream));
+}
+
 lb_status lb_coo_row_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
                              cudaStream_t stream) {
     if (m < 0 || nnz < 0 || (m == 0 && nnz != 0) || !row_offsets || !d_status || (nnz > 0 && !row_idx))

@@ -220,6 +220,11 @@ cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, cons
                         const int *row_end, const int *ci, const void *values, const float *B, float *C,
                         int *carry_row, float *carry_val, cudaStream_t st);
 
+// Single-source shortest paths over a CSR graph (w null: unit weights); allocates its
+// workspace with cudaMallocAsync and synchronizes the stream once or twice per iteration.
+cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *w, int source, float *dist,
+                     int *iterations, cudaStream_t st);
+
 // Row offsets (m + 1) of a row-sorted COO matrix; *d_status gets 1 (row out of range) | 2
 // (rows decrease) | 0.
 cudaError_t launch_coo_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
@@ -227,6 +232,10 @@ cudaError_t launch_coo_offsets(int m, int nnz, const int *row_idx, int *row_offs
 
 cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
                             int *d_status, cudaStream_t stream);
+
+// Exclusive scan of n ints (in place allowed); `sums` holds scan_scratch_ints(n) ints.
+cudaError_t exclusive_scan(const int *in, int *out, long long n, int *sums, cudaStream_t st);
+long long scan_scratch_ints(long long n);
 
 // Device properties of the current device (cached).
 int current_sm_count();

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in,
 }
 
 // Exclusive scan of n ints; `sums` needs ceil(n / 2048) ints of scratch.
-static cudaError_t exclusive_scan(const int *in, int *out, long long n, int *sums, cudaStream_t st) {
+cudaError_t exclusive_scan(const int *in, int *out, long long n, int *sums, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int nb = static_cast<int>((n + kScanChunk - 1) / kScanChunk);
     scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, sums);
@@ -111,7 +111,7 @@ static cudaError_t exclusive_scan(const int *in, int *out, long long n, int *sum
     return cudaGetLastError();
 }
 
-static long long scan_scratch_ints(long long n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
+long long scan_scratch_ints(long long n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
 
 // ------------------------------------------------------------------------------------------
 // Radix sort of (key, value) pairs by key, stable.

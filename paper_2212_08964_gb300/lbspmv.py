@@ -35,6 +35,7 @@ __all__ = [
     "validate_csr",
     "coo_row_offsets",
     "calibrate",
+    "sssp",
     "device_error",
     "set_profile_events",
     "SCHEDULES",
@@ -117,6 +118,7 @@ def _declare(lib):
         "lb_spmm_planned": [_P, _P, _P, _I, _I, _P, _P, _P],
         "lb_coo_row_offsets": [_I, _I, _P, _P, _P, _P],
         "lb_calibrate": [ctypes.POINTER(Calibration), _P],
+        "lb_sssp": [_I, _I, _P, _P, _P, _I, _P, ctypes.POINTER(_I), _P],
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -510,6 +512,24 @@ def coo_row_offsets(row_idx, m: int, stream=None):
     _check(lib.lb_coo_row_offsets(m, row_idx.numel(), _ptr(row_idx) if row_idx.numel() else None, _ptr(ro),
                                   _ptr(status), _stream(stream)), "lb_coo_row_offsets")
     return ro, int(status.item())
+
+
+def sssp(row_offsets, col_idx, weights=None, source: int = 0, out=None, stream=None):
+    """Shortest-path distances from `source` over a CSR graph (lb_sssp); weights None: unit
+    weights (BFS levels).  Returns (dist float32 tensor, frontier iterations)."""
+    lib = ensure_loaded()
+    _need(row_offsets, torch.int32, "row_offsets")
+    _need(col_idx, torch.int32, "col_idx")
+    n = row_offsets.numel() - 1
+    nnz = col_idx.numel()
+    if weights is not None:
+        _need(weights, torch.float32, "weights", nnz)
+    dist = torch.empty(n, dtype=torch.float32, device=row_offsets.device) if out is None else out
+    _need(dist, torch.float32, "dist", n)
+    it = _I()
+    _check(lib.lb_sssp(n, nnz, _ptr(row_offsets), _ptr(col_idx) if nnz else None, _ptr(weights), int(source),
+                       _ptr(dist), ctypes.byref(it), _stream(stream)), "lb_sssp")
+    return dist, it.value
 
 
 def calibrate(stream=None) -> dict:
