@@ -317,8 +317,8 @@ lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *
  * values, or NULL for unit weights (dist = BFS level).  dist (n floats, device) receives the
  * distances (+inf when unreachable); *iterations (host) the number of frontier iterations.
  * FP32 sums: each distance is the minimum over paths of the FP32 sum along the path.
- * Allocates its workspace (about 16 bytes per vertex) and synchronizes `stream` once or twice
- * per iteration.  Negative weights are not supported (the iteration count is capped at n + 1).
+ * Allocates its workspace (about 16 bytes per vertex) and synchronizes `stream` once per
+ * iteration.  Negative weights are not supported (the iteration count is capped at n + 1).
  */
 lb_status lb_sssp(int n, int nnz, const int *row_offsets, const int *col_idx, const float *weights,
                   int source, float *dist, int *iterations, cudaStream_t stream);

@@ -5,7 +5,8 @@
 // Space", the SSSP listing): every edge of the current frontier is an atom; relaxing it
 // computes the neighbour's tentative distance, lowers the neighbour's distance with an
 // atomic minimum, and adds the neighbour to the next frontier when the distance dropped; the
-// host loops until the frontier is empty.  Here the frontier's edges are split evenly over
+// host loops until the frontier is empty (one synchronization per iteration, to read the next
+// frontier's size).  Here the frontier's edges are split evenly over
 // the threads (the work-oriented schedule applied to the frontier): the frontier vertices'
 // degrees are scanned, and thread e relaxes edge e, finding its vertex by a binary search
 // over the scan.  A vertex enters the next frontier once per iteration (a stamp with the
@@ -41,11 +42,11 @@ __global__ void frontier_degrees_kernel(int fsize, const int *__restrict__ front
 }
 
 // Relax edges [0, total) of the frontier; pre[i] = first edge of frontier vertex i.
-__global__ void __launch_bounds__(kGraphThreads) relax_kernel(int fsize, long long total, int iter,
-                                                              const int *__restrict__ frontier,
+__global__ void __launch_bounds__(kGraphThreads) relax_kernel(int fsize, int iter, const int *__restrict__ frontier,
                                                               const int *__restrict__ pre, const int *__restrict__ ro,
                                                               const int *__restrict__ ci, const float *__restrict__ w,
                                                               float *dist, int *stamp, int *next, int *next_count) {
+    const long long total = __ldg(pre + fsize);  // the frontier's edge count (end of the scan)
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
         int lo = 0, hi = fsize - 1;  // last i with pre[i] <= e
@@ -102,15 +103,11 @@ cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *
         // pre[fsize] = 0 then scan fsize + 1 entries: pre[fsize] is the frontier's edge count.
         if ((e = cudaMemsetAsync(pre + fsize, 0, sizeof(int), st)) != cudaSuccess) break;
         if ((e = exclusive_scan(pre, pre, static_cast<long long>(fsize) + 1, sums, st)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(h_count, pre + fsize, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(d_count, 0, sizeof(int), st)) != cudaSuccess) break;
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
-        const long long total = *h_count;
-        if (total > 0) {
-            relax_kernel<<<blocks(total), kGraphThreads, 0, st>>>(fsize, total, iter, f_cur, pre, ro, ci, w, dist,
-                                                                  stamp, f_next, d_count);
-            if ((e = cudaGetLastError()) != cudaSuccess) break;
-        }
+        // The edge count stays on the device; the relaxation reads it and strides over it.
+        relax_kernel<<<sms * 16, kGraphThreads, 0, st>>>(fsize, iter, f_cur, pre, ro, ci, w, dist, stamp, f_next,
+                                                         d_count);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
         fsize = *h_count;

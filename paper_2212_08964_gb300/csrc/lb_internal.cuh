@@ -221,7 +221,7 @@ cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, cons
                         int *carry_row, float *carry_val, cudaStream_t st);
 
 // Single-source shortest paths over a CSR graph (w null: unit weights); allocates its
-// workspace with cudaMallocAsync and synchronizes the stream once or twice per iteration.
+// workspace with cudaMallocAsync and synchronizes the stream once per iteration.
 cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *w, int source, float *dist,
                      int *iterations, cudaStream_t st);
 

@@ -313,3 +313,21 @@ def test_calibrate(lb):
     assert 1e10 < c["gathers_per_s"] < 5e12
     assert 100 < c["read_GBps"] < 20000
     assert 100 < c["copy_GBps"] < 20000
+
+
+def test_one_row_spanning_thousands_of_tiles(lb, orc):
+    """A 5M-entry row between two short rows: its partial sums are carried out of ~2500 tiles
+    and combined by one fixup run."""
+    rng = np.random.default_rng(123)
+    a = synth.csr_from_row_lengths(rng, 6_000_000, np.array([3, 5_000_000, 2]))
+    x = vec(a.n, 124)
+    ro, ci, v = to_dev(a)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    assert plan.info()["num_tiles"] > 2000
+    y = plan.spmv(ci, v, dev(x))
+    y1 = lb.spmv(ro, ci, v, dev(x))
+    torch.cuda.synchronize()
+    scale = orc.row_absdot(a.row_offsets, a.col_idx, a.values, x)
+    ref = orc.spmv(a.row_offsets, a.col_idx, a.values, x)
+    check_bound(y.cpu().numpy(), ref, scale, TOL32)
+    assert torch.equal(y, y1)
