@@ -57,7 +57,8 @@ typedef enum {
     LB_SCHED_WARP_MAPPED = 2,   /* group-mapped with a 32-lane group (Ch.4 "Warp- and block-level") */
     LB_SCHED_BLOCK_MAPPED = 3,  /* group-mapped with the whole block as the group */
     LB_SCHED_GROUP_MAPPED = 4,  /* group-mapped, group_size in {4, 8, 16, 32} */
-    LB_SCHED_MERGE_PATH = 5     /* work-oriented merge-path (Alg. alg:work-oriented) */
+    LB_SCHED_MERGE_PATH = 5,    /* work-oriented merge-path (Alg. alg:work-oriented) */
+    LB_SCHED_NONZERO_SPLIT = 6  /* work-oriented, nonzeros only (Ch.3 "Work-Oriented"); plans only */
 } lb_schedule;
 
 typedef enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 } lb_dtype;

@@ -31,6 +31,7 @@ SOURCES = [
     "lb_spmm.cu",
     "lb_calibrate.cu",
     "lb_graph.cu",
+    "lb_nzsplit.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -48,7 +48,7 @@ bool merge_shape_ok(int threads, int ipt) {
 
 bool dtype_ok(lb_dtype d) { return d == LB_F32 || d == LB_BF16 || d == LB_F16; }
 
-bool sched_ok(lb_schedule s) { return s >= LB_SCHED_AUTO && s <= LB_SCHED_MERGE_PATH; }
+bool sched_ok(lb_schedule s) { return s >= LB_SCHED_AUTO && s <= LB_SCHED_NONZERO_SPLIT; }
 
 // Resolve a requested schedule and tuning into concrete values, or report an invalid request.
 bool resolve(int m, int n, int nnz, lb_schedule s, const lb_tuning *t, lb_schedule *out_s, lb_tuning *out_t) {
@@ -91,6 +91,9 @@ bool resolve(int m, int n, int nnz, lb_schedule s, const lb_tuning *t, lb_schedu
         case LB_SCHED_GROUP_MAPPED:
             if (r.group_size == 0) r.group_size = 32;
             if (r.group_size != 4 && r.group_size != 8 && r.group_size != 16 && r.group_size != 32) return false;
+            break;
+        case LB_SCHED_NONZERO_SPLIT:
+            r = lb_tuning{0, 0, 0};  // fixed: 256 threads x 8 nonzeros per tile
             break;
         default:
             return false;
@@ -151,6 +154,11 @@ struct lb_plan {
     int bucket_shift = 0;  // 0: one L2-sized bucket (CSR order, gathered through perm)
     int *bucket_pos = nullptr, *bucket_perm = nullptr;
     float *pv = nullptr;  // per call: values[k] * g[row(k)] in bucket order (nnz floats)
+    // Nonzero splitting (that schedule only): rows of each tile's first and last nonzero, and
+    // two carries per tile.
+    int G_nz = 0;
+    int *nz_first = nullptr, *nz_last = nullptr, *nz_carry_row = nullptr;
+    float *nz_carry_val = nullptr;
     // SpMM carries, allocated on first use and grown with the number of columns.
     int *mm_carry_row = nullptr;
     float *mm_carry_val = nullptr;
@@ -185,6 +193,12 @@ static void release_transpose(lb_plan *p) {
 
 static void free_plan_arrays(lb_plan *p) {
     release_transpose(p);
+    int *nz_ints[] = {p->nz_first, p->nz_last, p->nz_carry_row};
+    for (int *q : nz_ints)
+        if (q) cudaFree(q);
+    if (p->nz_carry_val) cudaFree(p->nz_carry_val);
+    p->nz_first = p->nz_last = p->nz_carry_row = nullptr;
+    p->nz_carry_val = nullptr;
     if (p->mm_carry_row) cudaFree(p->mm_carry_row);
     if (p->mm_carry_val) cudaFree(p->mm_carry_val);
     p->mm_carry_row = nullptr;
@@ -333,6 +347,14 @@ lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_sched
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_row, zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_nz, zero, sizeof(int), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && p->sched == LB_SCHED_NONZERO_SPLIT && nnz > 0) {
+        const int T = nzsplit_tile_nonzeros();
+        p->G_nz = static_cast<int>((static_cast<long long>(nnz) + T - 1) / T);
+        const size_t g = static_cast<size_t>(p->G_nz);
+        if ((e = dmalloc(&p->nz_first, g)) == cudaSuccess && (e = dmalloc(&p->nz_last, g)) == cudaSuccess &&
+            (e = dmalloc(&p->nz_carry_row, 2 * g)) == cudaSuccess && (e = dmalloc(&p->nz_carry_val, 2 * g)) == cudaSuccess)
+            e = launch_nz_partition(p->G_nz, m, nnz, p->ro, p->nz_first, p->nz_last, stream);
+    }
     if (e != cudaSuccess) {
         free_plan_arrays(p);
         delete p;
@@ -374,6 +396,9 @@ lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *valu
     if (!y || (p->nnz > 0 && (!col_idx || !values || !x))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return from_cuda(cudaMemsetAsync(y, 0, static_cast<size_t>(p->m) * sizeof(float), stream));
+    if (p->sched == LB_SCHED_NONZERO_SPLIT)
+        return from_cuda(launch_nzsplit(vdt, p->G_nz, p->m, p->nnz, p->nz_first, p->nz_last, p->ro, col_idx, values, x,
+                                        y, p->nz_carry_row, p->nz_carry_val, stream));
     if (p->sched != LB_SCHED_MERGE_PATH)
         return from_cuda(launch_mapped(p->sched, p->tune, vdt, p->m, p->ro, col_idx, values, x, y, stream));
     int *err = device_error_word();

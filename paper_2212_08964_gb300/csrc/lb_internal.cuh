@@ -220,6 +220,16 @@ cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, cons
                         const int *row_end, const int *ci, const void *values, const float *B, float *C,
                         int *carry_row, float *carry_val, cudaStream_t st);
 
+// Nonzero splitting: tiles of nzsplit_tile_nonzeros() nonzeros; first_row / last_row[G] hold
+// the rows of each tile's first and last nonzero; the SpMV clears y, writes rows with nonzeros
+// and fixes up 2 * G carries.
+int nzsplit_tile_nonzeros();
+cudaError_t launch_nz_partition(int G, int m, int nnz, const int *ro, int *first_row, int *last_row,
+                                cudaStream_t st);
+cudaError_t launch_nzsplit(lb_dtype vdt, int G, int m, int nnz, const int *first_row, const int *last_row,
+                           const int *ro, const int *ci, const void *values, const float *x, float *y,
+                           int *carry_row, float *carry_val, cudaStream_t st);
+
 // Single-source shortest paths over a CSR graph (w null: unit weights); allocates its
 // workspace with cudaMallocAsync and synchronizes the stream once per iteration.
 cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *w, int source, float *dist,

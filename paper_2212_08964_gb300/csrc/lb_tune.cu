@@ -27,6 +27,7 @@ std::vector<Candidate> all_candidates() {
     c.push_back({LB_SCHED_WARP_MAPPED, {0, 0, 32}});
     for (int gs : {4, 8, 16}) c.push_back({LB_SCHED_GROUP_MAPPED, {0, 0, gs}});
     for (int th : {128, 256}) c.push_back({LB_SCHED_BLOCK_MAPPED, {th, 0, 0}});
+    c.push_back({LB_SCHED_NONZERO_SPLIT, {0, 0, 0}});
     return c;
 }
 

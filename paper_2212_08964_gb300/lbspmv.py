@@ -59,6 +59,7 @@ SCHEDULES = {
     "block_mapped": 3,
     "group_mapped": 4,
     "merge_path": 5,
+    "nonzero_split": 6,
 }
 _SCHED_NAMES = {v: k for k, v in SCHEDULES.items()}
 # (threads, items per thread) shapes of the merge-path kernel compiled into the library.

@@ -87,7 +87,7 @@ def test_tune_measures_every_candidate_and_the_tuned_plan_is_correct(lb, orc):
         assert all(r["ms"] > 0 for r in res)
         assert [r["ms"] for r in res] == sorted(r["ms"] for r in res)
         assert {r["schedule"] for r in res} == {"merge_path", "thread_mapped", "warp_mapped", "group_mapped",
-                                                 "block_mapped"}
+                                                 "block_mapped", "nonzero_split"}
         plan = autotune.plan_for(ro, a.n, t)
         assert plan.info()["schedule"] == res[0]["schedule"]
         y = plan.spmv(ci, v, dev(x))

@@ -31,7 +31,7 @@ def _ref(orc, a, x, values=None):
 def test_worked_example_exact(lb):
     f = load("worked_example_4x4.txt")
     a = synth.CSR(4, 4, f["row_offsets"].astype(np.int32), f["col_idx"].astype(np.int32), f["values"].astype(np.float32))
-    for sched in ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped"]:
+    for sched in ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped", "nonzero_split"]:
         y, _ = _run(lb, a, f["x"].astype(np.float32), sched)
         assert np.array_equal(y, f["y"]), sched
 
@@ -72,7 +72,7 @@ def test_mapped_schedules_powerlaw_4k(lb, orc, sched, tune):
     check_bound(y, ref, scale, TOL32)
 
 
-@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped"])
+@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped", "nonzero_split"])
 def test_exact_special_cases(lb, sched):
     rng = np.random.default_rng(5)
     n = 3000
@@ -91,7 +91,7 @@ def test_exact_special_cases(lb, sched):
     assert np.array_equal(y, x[p])
 
 
-@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped"])
+@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped", "nonzero_split"])
 def test_integer_values_bit_exact(lb, orc, sched):
     rng = np.random.default_rng(6)
     a = synth.powerlaw_csr(20_000, 20_000, 300_000, 1.3, 20_000, seed=31)
@@ -127,7 +127,7 @@ def test_empty_rows_and_no_nonzeros(lb, orc):
     a = synth.csr_from_row_lengths(rng, 5000, lengths)
     x = vec(a.n, 105)
     ref, scale = _ref(orc, a, x)
-    for sched in ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped"]:
+    for sched in ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped", "nonzero_split"]:
         y, _ = _run(lb, a, x, sched)
         check_bound(y, ref, scale, TOL32)
         assert np.all(y[lengths == 0] == 0)
@@ -182,7 +182,7 @@ def test_auto_rule_and_plain_call(lb, orc):
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
-@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped", "block_mapped"])
+@pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "nonzero_split"])
 def test_half_precision_values(lb, orc, dtype, sched):
     a = workload("powerlaw_4k")
     x = vec(a.n, 108)
@@ -198,7 +198,7 @@ def test_deterministic(lb):
     a = workload("powerlaw_4k")
     ro, ci, v = to_dev(a)
     x = dev(vec(a.n, 109))
-    for sched in ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped"]:
+    for sched in ["merge_path", "thread_mapped", "warp_mapped", "block_mapped", "group_mapped", "nonzero_split"]:
         plan = lb.Plan(ro, a.n, a.nnz, schedule=sched)
         y1 = plan.spmv(ci, v, x)
         y2 = plan.spmv(ci, v, x)
@@ -247,6 +247,9 @@ def test_full_size_powerlaw_4m(lb, orc):
     mx, med = check_bound(y1.cpu().numpy(), ref, scale, TOL32)
     print(f"powerlaw_4m FP32: max rel err {mx:.3e} median {med:.3e}")
     assert lb.device_error() == 0
+    y3 = lb.Plan(ro, a.n, a.nnz, schedule="nonzero_split").spmv(ci, v, dev(x))
+    torch.cuda.synchronize()
+    check_bound(y3.cpu().numpy(), ref, scale, TOL32)
 
 
 def test_full_size_stencil(lb, orc):
@@ -326,8 +329,10 @@ def test_one_row_spanning_thousands_of_tiles(lb, orc):
     assert plan.info()["num_tiles"] > 2000
     y = plan.spmv(ci, v, dev(x))
     y1 = lb.spmv(ro, ci, v, dev(x))
+    y2 = lb.Plan(ro, a.n, a.nnz, schedule="nonzero_split").spmv(ci, v, dev(x))
     torch.cuda.synchronize()
     scale = orc.row_absdot(a.row_offsets, a.col_idx, a.values, x)
     ref = orc.spmv(a.row_offsets, a.col_idx, a.values, x)
     check_bound(y.cpu().numpy(), ref, scale, TOL32)
+    check_bound(y2.cpu().numpy(), ref, scale, TOL32)
     assert torch.equal(y, y1)
