@@ -13,7 +13,12 @@ A shape class is computed on the host from the row lengths:
 * ``size``: log2 of the work items m + nnz (rounded down);
 * ``mean``: log2 of the mean row length nnz / m, in half-octave steps;
 * ``skew``: the longest row over the mean row length, bucketed to 1, 4, 32, 256 and above;
+* ``lrb``: the logarithmic radix bin (Ch.3 Sec. "Binning and Reordering") of row lengths that
+  holds the most nonzeros;
 * ``dtype``: the value type.
+
+Without a table entry, ``choose_by_roofline`` picks the schedule family that a roofline model
+of the measured ceilings (``lbspmv.calibrate``) predicts fastest.
 
 Batches are classed by the batch count and total work (log2), and the dominant member class.
 The table is a plain dict that round-trips through JSON (``save`` / ``load``).
@@ -29,9 +34,12 @@ import numpy as np
 
 from . import lbspmv
 
-__all__ = ["shape_class", "batch_class", "Table", "tune", "tune_batched", "choose", "plan_for"]
+__all__ = ["shape_class", "lrb_bins", "batch_class", "Table", "tune", "tune_batched", "choose", "plan_for", "predict",
+           "choose_by_roofline"]
 
 _SKEW_EDGES = (1.5, 4.0, 32.0, 256.0)
+# Loaded latency of one dependent gather, for the critical path of row-per-thread schedules.
+_GATHER_LATENCY_S = 1.0e-6
 _DTYPE_NAMES = {0: "f32", 1: "bf16", 2: "f16"}
 
 
@@ -40,8 +48,23 @@ def _row_lengths(row_offsets) -> np.ndarray:
     return np.diff(ro)
 
 
+def lrb_bins(row_offsets) -> np.ndarray:
+    """Logarithmic radix binning of the rows (Ch.3 Sec. "Binning and Reordering"): the share
+    of the nonzeros held by rows of length in [2^b, 2^(b+1)), for b = 0..31 (empty rows hold
+    none)."""
+    lengths = _row_lengths(row_offsets)
+    nz = lengths[lengths > 0]
+    out = np.zeros(32)
+    if nz.size:
+        b = np.floor(np.log2(nz)).astype(np.int64)
+        np.add.at(out, b, nz.astype(np.float64))
+        out /= out.sum()
+    return out
+
+
 def shape_class(row_offsets, dtype: str = "f32") -> str:
-    """Class key of a CSR matrix from its (host) row offsets."""
+    """Class key of a CSR matrix from its (host) row offsets: work size, mean row length, skew,
+    the LRB bin holding the most nonzeros, and the value type."""
     lengths = _row_lengths(row_offsets)
     m = int(lengths.shape[0])
     nnz = int(lengths.sum()) if m else 0
@@ -50,7 +73,42 @@ def shape_class(row_offsets, dtype: str = "f32") -> str:
     mean_b = int(math.floor(2.0 * math.log2(mean))) if mean > 0 else -99
     skew = (float(lengths.max()) / mean) if mean > 0 else 0.0
     skew_b = sum(1 for e in _SKEW_EDGES if skew >= e)
-    return f"size{size}-mean{mean_b}-skew{skew_b}-{dtype}"
+    lrb = int(np.argmax(lrb_bins(row_offsets))) if nnz else -1
+    return f"size{size}-mean{mean_b}-skew{skew_b}-lrb{lrb}-{dtype}"
+
+
+def predict(row_offsets, n: int, calibration: dict, value_bytes: int = 4) -> dict:
+    """Roofline estimate of the SpMV time of each schedule family from the measured ceilings
+    (``lbspmv.calibrate()``), in seconds.
+
+    - Streamed bytes: values and column indices per nonzero, offsets and y per row.
+    - Work-oriented schedules (merge path, nonzero splitting) are bound by the larger of the
+      sector requests (one per random gather plus the streamed bytes / 32) at the measured
+      gather rate, and the streamed bytes at the measured read bandwidth.  Nonzero splitting
+      also clears y.
+    - Row-per-thread and row-per-warp schedules pay the same, or the critical path of their
+      longest row of dependent gathers (per thread, or per lane of a warp), whichever is longer.
+    """
+    lengths = _row_lengths(row_offsets)
+    m = int(lengths.shape[0])
+    nnz = int(lengths.sum()) if m else 0
+    streamed = nnz * (value_bytes + 4) + 8 * m + 4
+    rate = float(calibration["gathers_per_s"])
+    bw = float(calibration["read_GBps"]) * 1e9
+    balanced = max((nnz + streamed / 32.0) / rate, streamed / bw)
+    longest = int(lengths.max()) if m else 0
+    return {
+        "merge_path": balanced,
+        "nonzero_split": balanced + 4.0 * m / bw,
+        "thread_mapped": max(balanced, longest * _GATHER_LATENCY_S),
+        "warp_mapped": max(balanced, math.ceil(longest / 32) * _GATHER_LATENCY_S),
+    }
+
+
+def choose_by_roofline(row_offsets, n: int, calibration: dict, value_bytes: int = 4) -> str:
+    """The schedule family with the smallest ``predict`` time (ties go to merge path)."""
+    t = predict(row_offsets, n, calibration, value_bytes)
+    return min(t, key=lambda k: (t[k], k != "merge_path"))
 
 
 def batch_class(ms, nnzs, row_offsets_concat, dtype: str = "f32") -> str:

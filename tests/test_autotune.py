@@ -16,12 +16,12 @@ def _ro(lengths):
 
 def test_shape_class_fields():
     # 1000 rows of 8: work 9000 -> size 13; mean 8 -> 2*log2(8) = 6; skew 1 -> bucket 0.
-    assert autotune.shape_class(_ro([8] * 1000)) == "size13-mean6-skew0-f32"
+    assert autotune.shape_class(_ro([8] * 1000)) == "size13-mean6-skew0-lrb3-f32"
     # One long row among short ones: skew = max / mean.
     lengths = [1] * 999 + [1001]
     mean = sum(lengths) / 1000  # 2.0
     assert 1001 / mean >= 256
-    assert autotune.shape_class(_ro(lengths), "bf16").endswith("skew4-bf16")
+    assert autotune.shape_class(_ro(lengths), "bf16").endswith("skew4-lrb9-bf16")
     # Empty matrix and all-empty rows do not fail.
     assert autotune.shape_class(np.zeros(1, np.int32)).startswith("size0-")
     assert "mean-99" in autotune.shape_class(_ro([0] * 10))
@@ -115,3 +115,24 @@ def test_tune_batched(lb, orc):
     torch.cuda.synchronize()
     check_bound(y.cpu().numpy(), orc.batched_spmv(b, x), orc.batched_row_absdot(b, x), 1e-5)
     assert len(t.entries) == 1
+
+
+def test_lrb_bins():
+    b = autotune.lrb_bins(_ro([1, 1, 2, 3, 4, 0, 1000]))
+    # nonzeros: lengths 1,1 -> bin 0 (2); 2,3 -> bin 1 (5); 4 -> bin 2 (4); 1000 -> bin 9 (1000)
+    assert np.allclose(b[[0, 1, 2, 9]], np.array([2, 5, 4, 1000]) / 1011)
+    assert abs(b.sum() - 1) < 1e-12
+    assert not autotune.lrb_bins(_ro([0, 0])).any()
+
+
+def test_roofline_selector():
+    calib = {"gathers_per_s": 3e11, "read_GBps": 7000.0, "copy_GBps": 6500.0}
+    skewed = _ro([2] * 100000 + [500000])
+    uniform = _ro([7] * 400000)
+    t = autotune.predict(skewed, 1000, calib)
+    assert t["thread_mapped"] > 10 * t["merge_path"]  # one 500k row on one thread
+    assert autotune.choose_by_roofline(skewed, 1000, calib) == "merge_path"
+    tu = autotune.predict(uniform, 1000, calib)
+    assert tu["thread_mapped"] == tu["merge_path"]  # short rows: both at the same ceiling
+    assert autotune.choose_by_roofline(uniform, 1000, calib) == "merge_path"  # ties go to merge path
+    assert tu["nonzero_split"] > tu["merge_path"]
