@@ -498,7 +498,7 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
     if ((e = cudaMemsetAsync(out.col_offsets, 0, (static_cast<size_t>(n) + 1) * sizeof(int), st)) != cudaSuccess)
         return e;
     if (nnz == 0) return cudaSuccess;
-    const int nblocks = (nnz + kRsTile - 1) / kRsTile;
+    const int nblocks = static_cast<int>((static_cast<long long>(nnz) + kRsTile - 1) / kRsTile);
     const long long hist_n = 256ll * nblocks;
     long long scan_n = hist_n > static_cast<long long>(n) + 1 ? hist_n : static_cast<long long>(n) + 1;
     const size_t ints = static_cast<size_t>(nnz) * 3 + static_cast<size_t>(hist_n) +
@@ -583,7 +583,7 @@ cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket
                                 cudaStream_t st) {
     if (nnz <= 0) return cudaSuccess;
     cudaError_t e;
-    const int nblocks = (nnz + kRsTile - 1) / kRsTile;
+    const int nblocks = static_cast<int>((static_cast<long long>(nnz) + kRsTile - 1) / kRsTile);
     const long long hist_n = 256ll * nblocks;
     const size_t ints = 3 * static_cast<size_t>(nnz) + static_cast<size_t>(hist_n) +
                         static_cast<size_t>(scan_scratch_ints(hist_n));
