@@ -583,6 +583,7 @@ def run_ours(args):
         mixed["stencil7_160_forward"] = run_stencil_precision(lb, torch, dev)
         result["mixed_precision"] = mixed
         result["batched"] = run_batched(lb, torch, dev)
+        result["differentiable"] = run_differentiable(lb, torch, dev)
         result["spmm"] = run_spmm(lb, torch, dev, a, plan, ci, v, xd, y)
         result["sssp"] = run_sssp(lb, torch, dev, a, ro, ci)
     if args.extras and rank == 0:
@@ -629,6 +630,50 @@ def run_extras(lb, torch, dev):
         out[f"powerlaw_8m_{name}"] = {"forward_ms": ms, "forward_GBps": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9,
                                       "step_ms": ms_step}
     return out
+
+
+def run_differentiable(lb, torch, dev):
+    """The differentiable SpMV on the 1M-row log-normal matrix: the library step (forward saving
+    x[col], then dx and dvalues) with g given, and the autograd training step of the loss
+    0.5 ||A x - t||^2 (the loss and g = y - t are two small torch ops; the SpMV forward and
+    backward are the library's).  Bytes as for the main step."""
+    from paper_2212_08964_gb300 import synth
+
+    a = synth.workload("lognormal_1m")
+    rng = np.random.default_rng(4)
+    x = torch.from_numpy(synth.uniform_pm1(rng, a.n)).to(dev)
+    t = torch.from_numpy(synth.uniform_pm1(rng, a.m)).to(dev)
+    g = torch.from_numpy(synth.uniform_pm1(rng, a.m)).to(dev)
+    ro, ci = torch.from_numpy(a.row_offsets).to(dev), torch.from_numpy(a.col_idx).to(dev)
+    v = torch.from_numpy(a.values).to(dev)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    plan.build_transpose(ci)
+    y = torch.empty(a.m, device=dev)
+    dx = torch.empty(a.n, device=dev)
+    dv = torch.empty(a.nnz, device=dev)
+    xg = torch.empty(a.nnz, device=dev)
+
+    def step():
+        plan.spmv(ci, v, x, out=y, save_gathered=xg)
+        plan.backward(v, g, xg, dx=dx, dvalues=dv)
+
+    vt = v.clone().requires_grad_(True)
+    xt = x.clone().requires_grad_(True)
+
+    def train_step():
+        vt.grad = None
+        xt.grad = None
+        yy = lb.spmv_autograd(plan, ci, vt, xt)
+        loss = 0.5 * torch.sum((yy - t) ** 2)
+        loss.backward()
+
+    fwd_b, bwd_t_b, dv_b = step_bytes(a.m, a.n, a.nnz)
+    total = fwd_b + bwd_t_b + dv_b
+    ms = _time(torch, step, 50)
+    ms_train = _time(torch, train_step, 50)
+    return {"workload": f"lognormal_1m: m = n = {a.m}, nnz = {a.nnz}", "bytes_per_step": total,
+            "step_ms": ms, "step_GBps": total / (ms * 1e-3) / 1e9,
+            "autograd_train_step_ms": ms_train, "autograd_train_step_GBps": total / (ms_train * 1e-3) / 1e9}
 
 
 def run_stencil_precision(lb, torch, dev):

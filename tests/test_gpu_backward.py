@@ -108,7 +108,7 @@ def test_saved_gathers_unaligned_views(lb, orc):
 
 @pytest.mark.parametrize("name", ["worked", "powerlaw_4k", "skew", "wide", "stencil_small"])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
-@pytest.mark.parametrize("bucket_shift", [None, "10"])
+@pytest.mark.parametrize("bucket_shift", [None, "10", "12"])
 def test_two_pass_backward(lb, orc, monkeypatch, name, dtype, bucket_shift):
     """lb_spmv_backward: dx and dvalues from one CSR-order pass plus the gather-sum, equal bit
     for bit to lb_spmv_t and lb_spmv_dvalues_gathered, and to the oracle within tolerance."""
