@@ -189,6 +189,12 @@ lb_status lb_plan_transpose(const lb_plan *p, int *col_offsets, int *row_idx, in
  * column) and the product rounding are fixed, so dx is deterministic.  Requires
  * lb_plan_build_transpose.  g: m floats, dx: n floats (overwritten).  Not safe to run
  * concurrently with another lb_spmv_t / lb_spmv_backward on the same plan (shared scratch).
+ *
+ * CSC input.  A matrix A (m x n) given in CSC form (col_offsets[n+1], row_idx[nnz], values in
+ * CSC order) is A^T in CSR form.  A plan created from col_offsets with n_cols = m, with
+ * lb_plan_build_transpose(plan, row_idx), computes y = A x as lb_spmv_t(plan, values, x, y):
+ * merge-path over A's rows in the CSC view (Ch.4: merge-path over any format with an
+ * atoms-per-tile count; CSC as a format in Sec. "Implementing Sparse Data Structures").
  */
 lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
                     cudaStream_t stream);

@@ -30,6 +30,7 @@ __all__ = [
     "num_tiles",
     "Plan",
     "BatchedPlan",
+    "CscPlan",
     "SpMV",
     "spmv_autograd",
     "validate_csr",
@@ -399,6 +400,34 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class CscPlan:
+    """y = A x for A given in CSC form: col_offsets (n + 1), row_idx (nnz) and values in CSC
+    order.  A CSC matrix is its transpose in CSR form, so this is a Plan of A^T (n rows, m
+    columns) with its CSC view, which is A in CSR, built once; y = A x is that plan's
+    transposed product (lb_spmv_t): a streaming pass over A's columns scales each value by
+    x[col] (x is read in column order), then the merge-path gather-sum over A's rows adds them
+    up.  Merge-path serves any format with an atoms-per-tile count (Ch.4 Sec. "Merge-path load
+    balancing"; CSC as a format, Ch.4 Sec. "Implementing Sparse Data Structures").  With A's
+    columns sorted by row, the rows are summed in the order of A's CSR form, over the same
+    partition and with the same products as the CSR forward."""
+
+    def __init__(self, col_offsets: torch.Tensor, row_idx: torch.Tensor, m: int, nnz: int | None = None,
+                 schedule: str = "merge_path", threads: int = 0, items_per_thread: int = 0, stream=None):
+        self.plan = Plan(col_offsets, m, nnz, schedule=schedule, threads=threads, items_per_thread=items_per_thread,
+                         stream=stream)
+        self.plan.build_transpose(row_idx, stream=stream)
+        self.m = int(m)
+        self.n = self.plan.m
+        self.nnz = self.plan.nnz
+
+    def spmv(self, values, x, out=None, stream=None) -> torch.Tensor:
+        """y (m floats) = A x, x: n floats; values FP32, BF16 or FP16 in CSC order."""
+        return self.plan.spmv_t(values, x, out=out, stream=stream)
+
+    def close(self):
+        self.plan.close()
 
 
 class BatchedPlan:

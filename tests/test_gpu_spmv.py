@@ -276,6 +276,42 @@ def test_full_size_powerlaw_8m_half(lb, orc, dtype):
     print(f"powerlaw_8m {dtype}: vs FP32 values max {mx:.3e} median {med:.3e}")
 
 
+@pytest.mark.parametrize("name", ["powerlaw_4k", "stencil", "empty_rows", "few_columns"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("bucket_shift", [None, "10"])
+def test_csc_input(lb, orc, monkeypatch, name, dtype, bucket_shift):
+    """y = A x from A in CSC form (the oracle's stable transpose of the CSR matrix): within
+    tolerance of the oracle, and bit-equal to the CSR forward on the same matrix, whose
+    partition, products and summation order it shares."""
+    if bucket_shift:
+        monkeypatch.setenv("LBSPMV_VALUE_BUCKET_SHIFT", bucket_shift)
+    rng = np.random.default_rng(17)
+    if name == "powerlaw_4k":
+        a = workload("powerlaw_4k")
+    elif name == "stencil":
+        a = synth.stencil7_csr(9, seed=3)
+    elif name == "empty_rows":
+        lengths = rng.integers(0, 4, 5000)
+        lengths[:100] = 0
+        lengths[-300:] = 0
+        a = synth.csr_from_row_lengths(rng, 700, lengths)
+    else:  # many rows over few columns: long columns, and empty ones
+        a = synth.csr_from_row_lengths(rng, 40, rng.integers(0, 12, 20000))
+    co, ri, perm = orc.transpose(a.row_offsets, a.col_idx, a.n)
+    vals = a.values if dtype == torch.float32 else rounded(a.values, dtype)
+    v_csc = dev(a.values[perm]).to(dtype)
+    x = vec(a.n, 71)
+    cp = lb.CscPlan(dev(co), dev(ri), a.m)
+    y = cp.spmv(v_csc, dev(x))
+    plan = lb.Plan(dev(a.row_offsets), a.n, a.nnz, schedule="merge_path")
+    y_csr = plan.spmv(dev(a.col_idx), dev(a.values).to(dtype), dev(x))
+    torch.cuda.synchronize()
+    check_bound(y.cpu().numpy(), orc.spmv(a.row_offsets, a.col_idx, vals, x),
+                orc.row_absdot(a.row_offsets, a.col_idx, vals, x), TOL32)
+    assert torch.equal(y, y_csr)
+    assert lb.device_error() == 0
+
+
 @pytest.mark.parametrize("name", ["powerlaw_4k", "stencil", "empty_rows"])
 def test_coo_input(lb, orc, name):
     """COO (row-sorted) to CSR offsets bit-exact against counting; the COO matrix then runs
