@@ -1,4 +1,5 @@
 // lb_partition.cu -- merge-path partition, carry fixup, batched-plan helpers, validation.
+#include <climits>
 #include <mutex>
 
 #include "lb_internal.cuh"
@@ -217,23 +218,59 @@ __global__ void validate_offsets_kernel(int m, int nnz, const int *ro, int *stat
     }
 }
 
-// Column checks need row boundaries, which are only trustworthy when the offsets passed; the
-// kernel reads each row's range clamped to [0, nnz] so a broken offsets array cannot send it
-// out of bounds.  A warp takes a row and its lanes stride over the row's nonzeros (coalesced),
-// so a row of half a million entries costs one warp a few thousand steps, not one thread.
-__global__ void validate_columns_kernel(int m, int n, int nnz, const int *ro, const int *ci, int check_sorted,
-                                        int *status) {
+// Each warp checks a contiguous chunk of the nonzeros, 128 at a time (four per lane,
+// coalesced): the column range, and an increase over the predecessor except where a row
+// starts.  The row starts of each 128-entry window come from walking the row offsets
+// alongside (a merge of the two sorted sequences): the warp finds the first offset at or past
+// its chunk once by a binary search, then reads the offsets lane-parallel, window by window.
+// Row boundaries are only trustworthy when the offsets passed; whatever they hold, every read
+// stays inside ro[0..m] and the walk ends.
+__global__ void validate_columns_kernel(int m, int n, int nnz, const int *__restrict__ ro,
+                                        const int *__restrict__ ci, int check_sorted, int *status) {
+    constexpr int W = 4;  // 32-entry words per window
     const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
     const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    const long long chunk = ((static_cast<long long>(nnz) + warps - 1) / warps + 32 * W - 1) / (32 * W) * (32 * W);
+    const long long K0 = warp * chunk;
+    const long long K1 = K0 + chunk < nnz ? K0 + chunk : nnz;
     int bits = 0;
-    for (long long r = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; r < m; r += warps) {
-        long long b = ro[r], e = ro[r + 1];
-        b = b < 0 ? 0 : (b > nnz ? nnz : b);
-        e = e < b ? b : (e > nnz ? nnz : e);
-        for (long long k = b + lane; k < e; k += 32) {
-            const int c = ci[k];
-            if (c < 0 || c >= n) bits |= 8;
-            if (check_sorted && k > b && c <= ci[k - 1]) bits |= 16;
+    if (K0 < K1) {
+        long long r = 0, hi = m;  // first r in [0, m] with ro[r] >= K0
+        while (r < hi) {
+            const long long mid = (r + hi) >> 1;
+            if (__ldg(ro + mid) < K0) r = mid + 1;
+            else hi = mid;
+        }
+        for (long long K = K0; K < K1; K += 32 * W) {
+            int c[W], p[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const long long k = K + 32 * j + lane;
+                c[j] = k < K1 ? __ldg(ci + k) : 0;
+                p[j] = (k < K1 && k > 0) ? __ldg(ci + k - 1) : 0;
+            }
+            unsigned starts[W] = {};  // bit i of word j: a row starts at nonzero K + 32 j + i
+            for (;;) {
+                const long long rr = r + lane;
+                const long long s = rr <= m ? __ldg(ro + rr) : LLONG_MAX;
+                const long long d = s - K;
+                const bool in = d >= 0 && d < 32 * W;
+#pragma unroll
+                for (int j = 0; j < W; ++j)
+                    starts[j] |= __reduce_or_sync(0xffffffffu, (in && (d >> 5) == j) ? 1u << (d & 31) : 0u);
+                const int cnt = __popc(__ballot_sync(0xffffffffu, rr <= m && d < 32 * W));
+                r += cnt;
+                if (cnt < 32) break;
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const long long k = K + 32 * j + lane;
+                if (k < K1) {
+                    if (c[j] < 0 || c[j] >= n) bits |= 8;
+                    if (check_sorted && k > 0 && !((starts[j] >> lane) & 1u) && c[j] <= p[j]) bits |= 16;
+                }
+            }
         }
     }
     bits = __reduce_or_sync(0xffffffffu, bits);
@@ -298,8 +335,9 @@ cudaError_t launch_validate(int m, int n, int nnz, const int *ro, const int *ci,
     validate_offsets_kernel<<<blocks, 256, 0, stream>>>(m, nnz, ro, d_status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (m > 0 && nnz > 0) {
-        long long wblocks = (static_cast<long long>(m) + 7) / 8;  // a warp per row
-        if (wblocks > current_sm_count() * 16) wblocks = current_sm_count() * 16;
+        // Warps of 128-entry windows, at least 16 windows each until the grid is full.
+        long long wblocks = (static_cast<long long>(nnz) + 8 * 128 * 16 - 1) / (8 * 128 * 16);
+        if (wblocks > current_sm_count() * 8) wblocks = current_sm_count() * 8;
         validate_columns_kernel<<<static_cast<int>(wblocks), 256, 0, stream>>>(m, n, nnz, ro, ci, check_sorted,
                                                                                 d_status);
         e = cudaGetLastError();

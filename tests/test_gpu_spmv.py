@@ -228,6 +228,21 @@ def test_validate_csr(lb):
     badc[ro[r]], badc[ro[r] + 1] = badc[ro[r] + 1], badc[ro[r]]
     assert lb.validate_csr(dev(ro), dev(badc), a.n) == 16
     assert lb.validate_csr(dev(ro), dev(badc), a.n, check_sorted=False) == 0
+    # Rows longer than 32 entries are walked by a whole warp: errors deep inside one.
+    r = int(np.argmax(np.diff(ro) >= 64))
+    assert ro[r + 1] - ro[r] >= 64
+    badc = ci.copy()
+    badc[ro[r + 1] - 1] = a.n  # out of range at the row's end, still increasing
+    assert lb.validate_csr(dev(ro), dev(badc), a.n) == 8
+    badc = ci.copy()
+    badc[ro[r] + 40] = -1  # out of range and below its predecessor
+    assert lb.validate_csr(dev(ro), dev(badc), a.n) == 8 | 16
+    badc = ci.copy()
+    badc[ro[r] + 33], badc[ro[r] + 34] = badc[ro[r] + 34], badc[ro[r] + 33]
+    assert lb.validate_csr(dev(ro), dev(badc), a.n) == 16
+    badc = ci.copy()
+    badc[ro[r + 1] - 1] = badc[ro[r + 1] - 2]  # a repeated column at the row's end
+    assert lb.validate_csr(dev(ro), dev(badc), a.n) == 16
 
 
 # ------------------------------------------------------------------ full sizes
