@@ -584,6 +584,7 @@ def run_ours(args):
         result["mixed_precision"] = mixed
         result["batched"] = run_batched(lb, torch, dev)
         result["differentiable"] = run_differentiable(lb, torch, dev)
+        result["small_4k"] = run_small(lb, torch, dev)
         result["spmm"] = run_spmm(lb, torch, dev, a, plan, ci, v, xd, y)
         result["sssp"] = run_sssp(lb, torch, dev, a, ro, ci)
     if args.extras and rank == 0:
@@ -629,6 +630,34 @@ def run_extras(lb, torch, dev):
         ms_step = _time(torch, full, 10)
         out[f"powerlaw_8m_{name}"] = {"forward_ms": ms, "forward_GBps": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9,
                                       "step_ms": ms_step}
+    return out
+
+
+def run_small(lb, torch, dev):
+    """The small configuration (m = n = 4096, about 64k nonzeros), which launch latency bounds:
+    one planned forward per schedule, captured 50 times in a CUDA graph and replayed, in
+    microseconds per call, with the schedule the size rule picks."""
+    from paper_2212_08964_gb300 import synth
+
+    a = synth.workload("powerlaw_4k")
+    x = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(1), a.n)).to(dev)
+    ro, ci, v = (torch.from_numpy(t).to(dev) for t in (a.row_offsets, a.col_idx, a.values))
+    y = torch.empty(a.m, device=dev)
+    out = {"workload": f"powerlaw_4k: m = n = {a.m}, nnz = {a.nnz}",
+           "rule_choice": lb.Plan(ro, a.n, a.nnz, schedule="auto").info()["schedule"]}
+    for sched in ("merge_path", "thread_mapped", "warp_mapped", "block_mapped", "nonzero_split"):
+        plan = lb.Plan(ro, a.n, a.nnz, schedule=sched)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.spmv(ci, v, x, out=y)  # first call outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(50):
+                plan.spmv(ci, v, x, out=y)
+        out[f"{sched}_us"] = 1e3 * _time(torch, graph.replay, 20) / 50
+        del graph, plan
     return out
 
 
