@@ -582,6 +582,21 @@ def run_ours(args):
             mixed[f"{name}_speedup_vs_f32"] = f32_ms / ms_
         mixed["stencil7_160_forward"] = run_stencil_precision(lb, torch, dev)
         result["mixed_precision"] = mixed
+
+        # The opt-in backward without a CSC view: dx by float reductions into dx[col] in the
+        # CSR-order pass (not bit-reproducible), dvalues as in the step above.
+        def scatter_step():
+            plan.spmv(ci, v, xd, out=y, save_gathered=xg)
+            plan.backward_scatter(ci, v, gd, xg, dx=dx, dvalues=dv)
+
+        sc_ms = _time(torch, scatter_step, 20)
+        sc_bwd = _time(torch, lambda: plan.backward_scatter(ci, v, gd, xg, dx=dx, dvalues=dv), 20)
+        det_bwd = _time(torch, lambda: plan.backward(v, gd, xg, dx=dx, dvalues=dv), 20)
+        result["backward_scatter"] = {
+            "step_ms": sc_ms, "step_GBps": total_b / (sc_ms * 1e-3) / 1e9, "speedup_vs_step": f32_ms / sc_ms,
+            "backward_ms": sc_bwd, "deterministic_backward_ms": det_bwd,
+            "note": "opt-in lb_spmv_backward_scatter: dx by float reductions in L2, not bit-reproducible; "
+                    "no CSC view"}
         result["batched"] = run_batched(lb, torch, dev)
         result["differentiable"] = run_differentiable(lb, torch, dev)
         result["small_4k"] = run_small(lb, torch, dev)

@@ -236,6 +236,24 @@ lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, c
                            const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream);
 
 /*
+ * The backward without a CSC view, and not bit-reproducible: one streaming pass over the
+ * nonzeros in CSR order (the forward partition, as in lb_spmv_backward's first pass) adds
+ * every v[k] * g[row(k)] into dx[col_idx[k]] with a float reduction in L2, and, when dvalues
+ * is given, writes dvalues[k] = g[row(k)] * x_gathered[k] (bit-exact, as lb_spmv_backward).
+ * The additions into a column arrive in no fixed order, so dx can differ in its last bits from
+ * run to run; it stays within the FP32 bound of the transposed product (per column
+ * 1e-5 * sum_i |a_ij| |g_i|).  The dissertation computes no backward; this is the
+ * atomic-scatter alternative to the transposed SpMV of lb_spmv_backward, for callers that
+ * trade reproducibility for one pass and no CSC plan memory.
+ * col_idx: nnz ints; values: nnz of vdt; g: m floats; x_gathered: nnz floats from
+ * lb_spmv_planned_save (may be NULL when dvalues is NULL); dx: n floats, overwritten (zeroed,
+ * then accumulated); dvalues: nnz floats or NULL.  Needs only the plan's forward partition.
+ */
+lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
+                                   const float *g, const float *x_gathered, float *dx, float *dvalues,
+                                   cudaStream_t stream);
+
+/*
  * SpMM: C = A B with B dense (n x kc, row-major, FP32) and C (m x kc, row-major, FP32,
  * overwritten), over the plan's merge-path partition: the dissertation's SpMV with a loop over
  * the columns of B (Ch.4 Sec. "Application Space", the SpMM listing).  Each nonzero gathers a

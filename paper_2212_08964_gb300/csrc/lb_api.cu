@@ -571,6 +571,19 @@ lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, c
     return transposed_product(p, values, vdt, g, x_gathered, dx, dvalues, stream);
 }
 
+lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
+                                   const float *g, const float *x_gathered, float *dx, float *dvalues,
+                                   cudaStream_t stream) {
+    if (!p || !dtype_ok(vdt) || !dx) return LB_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!col_idx || !values || !g || (dvalues && !x_gathered))) return LB_ERR_INVALID_ARG;
+    if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
+    if (p->n == 0) return LB_OK;
+    cudaError_t e = cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream);
+    if (e != cudaSuccess || p->nnz == 0) return from_cuda(e);
+    return from_cuda(launch_csr_backward_scatter(vdt, p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, g,
+                                                 values, col_idx, dx, x_gathered, dvalues, stream));
+}
+
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
                           cudaStream_t stream) {
     if (!p) return LB_ERR_INVALID_ARG;

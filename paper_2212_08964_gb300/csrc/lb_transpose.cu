@@ -320,7 +320,28 @@ __device__ __forceinline__ void load_values(const V *src, bool vec, bool full, i
     }
 }
 
-template <typename V, int THREADS, int IPT>
+template <int IPT>
+__device__ __forceinline__ void load_ints(const int *src, bool vec, bool full, int j0, int nk, int (&o)[IPT]) {
+    if (full && vec) {
+#pragma unroll
+        for (int q = 0; q < IPT; q += 4) {
+            const int4 t = __ldcs(reinterpret_cast<const int4 *>(src + q));
+            o[q] = t.x;
+            o[q + 1] = t.y;
+            o[q + 2] = t.z;
+            o[q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) o[q] = (j0 + q >= 0 && j0 + q < nk) ? __ldcs(src + q) : 0;
+    }
+}
+
+// SCATTER: instead of the bucketed scaled values, add each v[k] * g[row(k)] into dx[col(k)]
+// with a float reduction in L2 (dx must start at zero).  No CSC view is needed; the sums of a
+// column then arrive in no fixed order, so dx is not bit-reproducible (it stays within the
+// FP32 tolerance of the transposed product).
+template <typename V, int THREADS, int IPT, bool SCATTER>
 __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, const int *__restrict__ tile_row,
                                                                const int *__restrict__ tile_nz,
                                                                const int *__restrict__ row_end,
@@ -328,7 +349,8 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
                                                                const V *__restrict__ values,
                                                                const int *__restrict__ bucket_pos,
                                                                float *__restrict__ pv, const float *__restrict__ xg,
-                                                               float *__restrict__ dv) {
+                                                               float *__restrict__ dv, const int *__restrict__ ci,
+                                                               float *__restrict__ dx_acc) {
     constexpr int T = THREADS * IPT;
     constexpr int WARPS = THREADS / 32;
     static_assert(IPT % 4 == 0, "slots move four at a time");
@@ -338,7 +360,8 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
     for (int i = threadIdx.x; i < T; i += THREADS) cnt[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool want_pv = pv != nullptr, want_dv = dv != nullptr;
+    const bool want_pv = !SCATTER && pv != nullptr, want_dv = dv != nullptr;
+    const bool vec_ci = (reinterpret_cast<uintptr_t>(ci) & 15u) == 0;
     // Slot 0 of every tile is 16-byte aligned in an array whose base is (4-byte elements) or
     // 8-byte aligned (2-byte values, moved four at a time).
     const bool vec_xg = (reinterpret_cast<uintptr_t>(xg) & 15u) == 0;
@@ -358,9 +381,10 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
         // the row-end staging and the scan: this thread's values and saved gathers (blocked)
         // and the bucket positions of the lane-consecutive scatter.
         float vv[IPT], xv[IPT];
-        int bp[IPT];
-        if (want_pv && mine) load_values<V, IPT>(values + k0 + j0, vec_v, full, j0, nk, vv);
+        int bp[IPT], cc[IPT];
+        if ((want_pv || SCATTER) && mine) load_values<V, IPT>(values + k0 + j0, vec_v, full, j0, nk, vv);
         if (want_dv && mine) load_values<float, IPT>(xg + k0 + j0, vec_xg, full, j0, nk, xv);
+        if (SCATTER && mine) load_ints<IPT>(ci + k0 + j0, vec_ci, full, j0, nk, cc);
         if (want_pv) {
 #pragma unroll
             for (int u = 0; u < IPT; ++u) {
@@ -403,6 +427,11 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
                 const int row = r0 + base + c[q];
                 gq[q] = (j0 + q >= 0 && j0 + q < nk && row < m) ? __ldg(g + row) : 0.f;
             }
+            if (SCATTER) {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if (j0 + q >= 0 && j0 + q < nk) atomicAdd(dx_acc + cc[q], vv[q] * gq[q]);
+            }
             if (want_pv) {
 #pragma unroll
                 for (int q = 0; q < IPT; q += 4)
@@ -436,10 +465,11 @@ __global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, con
     }
 }
 
-template <typename V>
+template <typename V, bool SCATTER>
 static cudaError_t launch_csr_backward_t(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
                                          const int *row_end, const float *g, const V *values, const int *bucket_pos,
-                                         float *pv, const float *xg, float *dv, cudaStream_t stream) {
+                                         float *pv, const float *xg, float *dv, const int *ci, float *dx_acc,
+                                         cudaStream_t stream) {
     // One wave of resident CTAs (the kernel loops over tiles).  A tile's slots: its items plus
     // a lead of up to 3 must fit.
     auto launch = [&](auto kern, int threads) -> cudaError_t {
@@ -449,11 +479,11 @@ static cudaError_t launch_csr_backward_t(int num_tiles, int m, int tile_items, c
         long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
         if (grid > num_tiles) grid = num_tiles;
         kern<<<static_cast<int>(grid), threads, 0, stream>>>(num_tiles, m, tile_row, tile_nz, row_end, g, values,
-                                                             bucket_pos, pv, xg, dv);
+                                                             bucket_pos, pv, xg, dv, ci, dx_acc);
         return cudaGetLastError();
     };
-    if (tile_items + 3 <= 2048) return launch(csr_backward_kernel<V, 256, 8>, 256);
-    if (tile_items + 3 <= 4096) return launch(csr_backward_kernel<V, 512, 8>, 512);
+    if (tile_items + 3 <= 2048) return launch(csr_backward_kernel<V, 256, 8, SCATTER>, 256);
+    if (tile_items + 3 <= 4096) return launch(csr_backward_kernel<V, 512, 8, SCATTER>, 512);
     return cudaErrorInvalidValue;
 }
 
@@ -464,15 +494,40 @@ cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_ite
     if ((pv != nullptr && values == nullptr) || (dv != nullptr && xg == nullptr)) return cudaErrorInvalidValue;
     switch (vdt) {
         case LB_F32:
-            return launch_csr_backward_t<float>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                static_cast<const float *>(values), bucket_pos, pv, xg, dv, stream);
+            return launch_csr_backward_t<float, false>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                       static_cast<const float *>(values), bucket_pos, pv, xg, dv,
+                                                       nullptr, nullptr, stream);
         case LB_BF16:
-            return launch_csr_backward_t<__nv_bfloat16>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                        static_cast<const __nv_bfloat16 *>(values), bucket_pos, pv,
-                                                        xg, dv, stream);
+            return launch_csr_backward_t<__nv_bfloat16, false>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                               static_cast<const __nv_bfloat16 *>(values), bucket_pos,
+                                                               pv, xg, dv, nullptr, nullptr, stream);
         case LB_F16:
-            return launch_csr_backward_t<__half>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                 static_cast<const __half *>(values), bucket_pos, pv, xg, dv, stream);
+            return launch_csr_backward_t<__half, false>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                        static_cast<const __half *>(values), bucket_pos, pv, xg, dv,
+                                                        nullptr, nullptr, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+                                        const int *tile_nz, const int *row_end, const float *g, const void *values,
+                                        const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream) {
+    if (num_tiles <= 0) return cudaSuccess;
+    if (values == nullptr || ci == nullptr || dx == nullptr || (dv != nullptr && xg == nullptr))
+        return cudaErrorInvalidValue;
+    switch (vdt) {
+        case LB_F32:
+            return launch_csr_backward_t<float, true>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                      static_cast<const float *>(values), nullptr, nullptr, xg, dv, ci,
+                                                      dx, stream);
+        case LB_BF16:
+            return launch_csr_backward_t<__nv_bfloat16, true>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                              static_cast<const __nv_bfloat16 *>(values), nullptr,
+                                                              nullptr, xg, dv, ci, dx, stream);
+        case LB_F16:
+            return launch_csr_backward_t<__half, true>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
+                                                       static_cast<const __half *>(values), nullptr, nullptr, xg, dv,
+                                                       ci, dx, stream);
     }
     return cudaErrorInvalidValue;
 }

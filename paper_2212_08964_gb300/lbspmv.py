@@ -117,6 +117,7 @@ def _declare(lib):
         "lb_spmv_planned_save": [_P, _P, _P, _I, _P, _P, _P, _P],
         "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _P],
         "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _P],
+        "lb_spmv_backward_scatter": [_P, _P, _P, _I, _P, _P, _P, _P, _P],
         "lb_spmm_planned": [_P, _P, _P, _I, _I, _P, _P, _P],
         "lb_coo_row_offsets": [_I, _I, _P, _P, _P, _P],
         "lb_calibrate": [ctypes.POINTER(Calibration), _P],
@@ -378,6 +379,28 @@ class Plan:
         _need(dvalues, torch.float32, "dvalues", self.nnz)
         _check(_lib.lb_spmv_backward(self._h, _ptr(values), _vdt(values), _ptr(g), _ptr(x_gathered), _ptr(dx),
                                      _ptr(dvalues), _stream(stream)), "lb_spmv_backward")
+        return dx, dvalues
+
+    def backward_scatter(self, col_idx, values, g, x_gathered=None, dx=None, dvalues=None, want_dvalues=True,
+                         stream=None):
+        """(dx, dvalues) in one CSR-order pass without a CSC view (lb_spmv_backward_scatter):
+        dx by float reductions into dx[col] (within tolerance, not bit-reproducible), dvalues
+        as ``backward`` (bit-exact; needs ``x_gathered``).  dvalues is None when not wanted."""
+        _need(col_idx, torch.int32, "col_idx", self.nnz)
+        _need(values, None, "values", self.nnz)
+        _need(g, torch.float32, "g", self.m)
+        dx = torch.empty(self.n, dtype=torch.float32, device=g.device) if dx is None else dx
+        _need(dx, torch.float32, "dx", self.n)
+        if want_dvalues:
+            _need(x_gathered, torch.float32, "x_gathered", self.nnz)
+            dvalues = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if dvalues is None else dvalues
+            _need(dvalues, torch.float32, "dvalues", self.nnz)
+        else:
+            dvalues = None
+        _check(_lib.lb_spmv_backward_scatter(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(g),
+                                             _ptr(x_gathered) if x_gathered is not None else None, _ptr(dx),
+                                             _ptr(dvalues) if dvalues is not None else None, _stream(stream)),
+               "lb_spmv_backward_scatter")
         return dx, dvalues
 
     def dvalues_gathered(self, g, x_gathered, out=None, stream=None) -> torch.Tensor:

@@ -269,6 +269,58 @@ def test_bucketed_value_permutation(lb, orc, monkeypatch):
         assert np.array_equal(perm, operm) and np.array_equal(ri, ori)
 
 
+@pytest.mark.parametrize("name", ["worked", "powerlaw_4k", "skew", "wide", "stencil_small"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_backward_scatter(lb, orc, name, dtype):
+    """lb_spmv_backward_scatter, with no CSC view: dx within tolerance of the oracle (its
+    additions into a column come in no fixed order), dvalues bit-exact; dx alone as well."""
+    a = _cases()[name]
+    ro, ci, v = to_dev(a, dtype)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    x, g = vec(a.n, 241), vec(a.m, 242)
+    xg = torch.empty(a.nnz, device="cuda")
+    plan.spmv(ci, v, dev(x), save_gathered=xg)
+    dx, dv = plan.backward_scatter(ci, v, dev(g), xg)
+    dx2, none = plan.backward_scatter(ci, v, dev(g), want_dvalues=False)
+    torch.cuda.synchronize()
+    assert none is None
+    vals = a.values if dtype == torch.float32 else rounded(a.values, dtype)
+    ref = orc.spmv_t(a.row_offsets, a.col_idx, vals, g, a.n)
+    scale = orc.col_absdot(a.row_offsets, a.col_idx, vals, g, a.n)
+    check_bound(dx.cpu().numpy(), ref, scale, TOL32, "columns")
+    check_bound(dx2.cpu().numpy(), ref, scale, TOL32, "columns")
+    assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+    assert lb.device_error() == 0
+
+
+def test_backward_scatter_unaligned_and_empty(lb, orc):
+    """Column indices, values and saved gathers at offsets that break 16-byte alignment; and a
+    matrix without nonzeros (dx all zero)."""
+    a = workload("powerlaw_4k")
+    x, g = vec(a.n, 243), vec(a.m, 244)
+    ro = dev(a.row_offsets)
+    ci_buf = torch.zeros(a.nnz + 4, dtype=torch.int32, device="cuda")
+    ci_buf[1: 1 + a.nnz] = dev(a.col_idx)
+    v_buf = torch.zeros(a.nnz + 4, device="cuda")
+    v_buf[3: 3 + a.nnz] = dev(a.values)
+    ci, v = ci_buf[1: 1 + a.nnz], v_buf[3: 3 + a.nnz]
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    xg_buf = torch.zeros(a.nnz + 4, device="cuda")
+    xg = xg_buf[2: 2 + a.nnz]
+    plan.spmv(ci, v, dev(x), save_gathered=xg)
+    dx, dv = plan.backward_scatter(ci, v, dev(g), xg)
+    torch.cuda.synchronize()
+    check_bound(dx.cpu().numpy(), orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n),
+                orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n), TOL32, "columns")
+    assert np.array_equal(dv.cpu().numpy(), orc.dvalues(a.row_offsets, a.col_idx, g, x).astype(np.float32))
+    empty = lb.Plan(torch.zeros(6, dtype=torch.int32, device="cuda"), 9, 0, schedule="merge_path")
+    dx0 = torch.full((9,), 7.0, device="cuda")
+    empty.backward_scatter(torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, device="cuda"),
+                           torch.ones(5, device="cuda"), want_dvalues=False, dx=dx0)
+    torch.cuda.synchronize()
+    assert torch.equal(dx0, torch.zeros(9, device="cuda"))
+
+
 def test_training_step_in_a_cuda_graph(lb, orc):
     """Forward saving its gathers plus the two-pass backward, captured once in a CUDA graph and
     replayed: the same bits as eager calls (no allocation or synchronization inside)."""
