@@ -57,7 +57,6 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     p.add_argument("--no-secondary", action="store_true",
                    help="skip the secondary lines (BF16/FP16 step, batched vs per-matrix)")
-    p.add_argument("--extras", action="store_true", help="also time the 8M-row matrix in FP32, BF16 and FP16")
     return p.parse_args(argv)
 
 
@@ -580,7 +579,9 @@ def run_ours(args):
             ms_ = step_ms(v.to(dt))
             mixed[f"{name}_step_ms"] = ms_
             mixed[f"{name}_speedup_vs_f32"] = f32_ms / ms_
+        mixed["tuned_" + args.workload] = run_tuned_precision(lb, torch, a, ro, ci, v, xd, gd, y, dx, dv, xg)
         mixed["stencil7_160_forward"] = run_stencil_precision(lb, torch, dev)
+        mixed["powerlaw_8m_forward"] = run_c5(lb, torch, dev)
         result["mixed_precision"] = mixed
 
         # The opt-in backward without a CSC view: dx by float reductions into dx[col] in the
@@ -602,8 +603,6 @@ def run_ours(args):
         result["small_4k"] = run_small(lb, torch, dev)
         result["spmm"] = run_spmm(lb, torch, dev, a, plan, ci, v, xd, y)
         result["sssp"] = run_sssp(lb, torch, dev, a, ro, ci)
-    if args.extras and rank == 0:
-        result["extras"] = run_extras(lb, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -617,34 +616,69 @@ def run_ours(args):
     return 0
 
 
-def run_extras(lb, torch, dev):
-    """The 8M-row power-law matrix (128M nonzeros): forward and the full step with FP32, BF16
-    and FP16 values."""
+def _tuned_plan(lb, torch, a, ro, dtype_name):
+    """A plan with the shipped GB300 table's configuration for the matrix's class and value
+    type (the size rule when the class is not in the table), and that configuration."""
+    from paper_2212_08964_gb300 import autotune
+
+    cfg = autotune.choose(a.row_offsets, autotune.default_table(), dtype_name)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule=cfg["schedule"], threads=cfg["threads"],
+                   items_per_thread=cfg["items_per_thread"], group_size=cfg["group_size"])
+    info = plan.info()
+    return plan, [info["schedule"], info["threads"], info["items_per_thread"], info["group_size"]]
+
+
+_DTYPES = (("f32", "float32", 4), ("bf16", "bfloat16", 2), ("f16", "float16", 2))
+
+
+def run_tuned_precision(lb, torch, a, ro, ci, v, xd, gd, y, dx, dv, xg):
+    """The step and the forward with each value type in the autotuned configuration of its
+    class (the shipped GB300 table): the shape that wins for narrow values differs."""
+    out = {}
+    for name, tname, _ in _DTYPES:
+        plan, shape = _tuned_plan(lb, torch, a, ro, name)
+        plan.build_transpose(ci)
+        vd = v.to(getattr(torch, tname))
+
+        def step():
+            plan.spmv(ci, vd, xd, out=y, save_gathered=xg)
+            plan.backward(vd, gd, xg, dx=dx, dvalues=dv)
+
+        out[name] = {"config": shape, "forward_ms": _time(torch, lambda: plan.spmv(ci, vd, xd, out=y), 20),
+                     "forward_save_ms": _time(torch, lambda: plan.spmv(ci, vd, xd, out=y, save_gathered=xg), 20),
+                     "backward_ms": _time(torch, lambda: plan.backward(vd, gd, xg, dx=dx, dvalues=dv), 20),
+                     "step_ms": _time(torch, step, 20)}
+        del plan
+    for name in ("bf16", "f16"):
+        out[f"{name}_forward_speedup_vs_f32"] = out["f32"]["forward_ms"] / out[name]["forward_ms"]
+        out[f"{name}_step_speedup_vs_f32"] = out["f32"]["step_ms"] / out[name]["step_ms"]
+    return out
+
+
+def run_c5(lb, torch, dev):
+    """The mixed-precision configuration: the 8M-row power-law matrix (128M nonzeros), the
+    forward with FP32, BF16 and FP16 values, in the default merge-path shape and in each value
+    type's autotuned configuration."""
     from paper_2212_08964_gb300 import synth
 
     out = {}
     a = synth.workload("powerlaw_8m")
-    rng = np.random.default_rng(6)
-    x = torch.from_numpy(synth.uniform_pm1(rng, a.n)).to(dev)
-    g = torch.from_numpy(synth.uniform_pm1(rng, a.m)).to(dev)
+    x = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(6), a.n)).to(dev)
     ro, ci = torch.from_numpy(a.row_offsets).to(dev), torch.from_numpy(a.col_idx).to(dev)
-    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
-    plan.build_transpose(ci)
     y = torch.empty(a.m, device=dev)
-    dx = torch.empty(a.n, device=dev)
-    dv = torch.empty(a.nnz, device=dev)
-    xg = torch.empty(a.nnz, device=dev)
-    for name, dt, vb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
-        v = torch.from_numpy(a.values).to(dev).to(dt)
-        ms = _time(torch, lambda: plan.spmv(ci, v, x, out=y), 20)
-
-        def full():
-            plan.spmv(ci, v, x, out=y, save_gathered=xg)
-            plan.backward(v, g, xg, dx=dx, dvalues=dv)
-
-        ms_step = _time(torch, full, 10)
-        out[f"powerlaw_8m_{name}"] = {"forward_ms": ms, "forward_GBps": spmv_bytes(a.m, a.n, a.nnz, vb) / (ms * 1e-3) / 1e9,
-                                      "step_ms": ms_step}
+    out["workload"] = f"powerlaw_8m: m = n = {a.m}, nnz = {a.nnz}"
+    base = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    for name, tname, vb in _DTYPES:
+        v = torch.from_numpy(a.values).to(dev).to(getattr(torch, tname))
+        ms = _time(torch, lambda: base.spmv(ci, v, x, out=y), 20)
+        plan, shape = _tuned_plan(lb, torch, a, ro, name)
+        ms_t = _time(torch, lambda: plan.spmv(ci, v, x, out=y), 20)
+        byts = spmv_bytes(a.m, a.n, a.nnz, vb)
+        out[name] = {"default_ms": ms, "tuned_config": shape, "tuned_ms": ms_t, "tuned_GBps": byts / (ms_t * 1e-3) / 1e9}
+        del plan, v
+    for name in ("bf16", "f16"):
+        out[f"{name}_speedup_vs_f32_tuned"] = out["f32"]["tuned_ms"] / out[name]["tuned_ms"]
+        out[f"{name}_speedup_vs_f32_default_shape"] = out["f32"]["default_ms"] / out[name]["default_ms"]
     return out
 
 

@@ -22,6 +22,10 @@ of the measured ceilings (``lbspmv.calibrate``) predicts fastest.
 
 Batches are classed by the batch count and total work (log2), and the dominant member class.
 The table is a plain dict that round-trips through JSON (``save`` / ``load``).
+
+``build_table`` tunes the standard synthetic workloads (FP32, BF16 and FP16 values, and the
+batch of 4096 matrices); ``python -m paper_2212_08964_gb300.autotune --out PATH`` runs it on the current
+GPU.  The package ships the table measured on a GB300 (``default_table``).
 """
 from __future__ import annotations
 
@@ -35,7 +39,7 @@ import numpy as np
 from . import lbspmv
 
 __all__ = ["shape_class", "lrb_bins", "batch_class", "Table", "tune", "tune_batched", "choose", "plan_for", "predict",
-           "choose_by_roofline"]
+           "choose_by_roofline", "build_table", "default_table", "DEFAULT_TABLE", "STANDARD_WORKLOADS"]
 
 _SKEW_EDGES = (1.5, 4.0, 32.0, 256.0)
 # Loaded latency of one dependent gather, for the critical path of row-per-thread schedules.
@@ -216,6 +220,48 @@ def tune_batched(ms, ns, nnzs, row_offsets_concat, col_idx_concat, values_concat
     return res
 
 
+# The table measured on a GB300 (sm_103a) by ``build_table`` over ``STANDARD_WORKLOADS``.
+DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tables", "gb300_sm103.json")
+STANDARD_WORKLOADS = ("powerlaw_4k", "powerlaw_4m", "stencil7_160", "lognormal_1m", "powerlaw_8m")
+
+
+def default_table() -> Table | None:
+    """The shipped GB300 table, or None when it is absent."""
+    return Table.load(DEFAULT_TABLE) if os.path.exists(DEFAULT_TABLE) else None
+
+
+def build_table(workloads=STANDARD_WORKLOADS, dtypes=("f32", "bf16", "f16"), batched=("batched_4096",), reps: int = 10,
+                table: Table | None = None, log=None) -> Table:
+    """Tune every workload in every value type (and every batch) on the current GPU and
+    record the winners by shape class."""
+    import torch
+
+    from . import synth
+
+    table = Table() if table is None else table
+    torch_dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    for name in workloads:
+        a = synth.workload(name)
+        x = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(0), a.n)).cuda()
+        ro, ci = torch.from_numpy(a.row_offsets).cuda(), torch.from_numpy(a.col_idx).cuda()
+        for dt in dtypes:
+            v = torch.from_numpy(a.values).cuda().to(torch_dt[dt])
+            res = tune(ro, ci, v, x, a.n, reps=reps, table=table)
+            if log:
+                log(f"{name} {dt}: {res[0]['schedule']} ({res[0]['threads']}, {res[0]['items_per_thread']}, "
+                    f"{res[0]['group_size']}) {res[0]['ms'] * 1e3:.1f} us")
+        del ro, ci, v, x, a
+    for name in batched:
+        b = synth.workload(name)
+        xs = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(0), int(b.ns.sum()))).cuda()
+        res = tune_batched(b.ms, b.ns, b.nnzs, torch.from_numpy(b.row_offsets).cuda(),
+                           torch.from_numpy(b.col_idx).cuda(), torch.from_numpy(b.values).cuda(), xs, reps=reps,
+                           table=table)
+        if log:
+            log(f"{name}: ({res[0]['threads']}, {res[0]['items_per_thread']}) {res[0]['ms'] * 1e3:.1f} us")
+    return table
+
+
 def choose(row_offsets, table: Table | None, dtype: str = "f32") -> dict:
     """The configuration for a matrix: the table's winner for its class, else the
     dissertation's size rule (schedule "auto")."""
@@ -228,3 +274,16 @@ def plan_for(row_offsets, n: int, table: Table | None, dtype: str = "f32", strea
     cfg = choose(row_offsets.cpu().numpy(), table, dtype)
     return lbspmv.Plan(row_offsets, n, schedule=cfg["schedule"], threads=cfg["threads"],
                        items_per_thread=cfg["items_per_thread"], group_size=cfg["group_size"], stream=stream)
+
+
+if __name__ == "__main__":
+    import argparse
+
+    p = argparse.ArgumentParser(description="Tune the standard workloads on this GPU and write the table.")
+    p.add_argument("--out", default=DEFAULT_TABLE)
+    p.add_argument("--reps", type=int, default=10)
+    args = p.parse_args()
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    t = build_table(reps=args.reps, log=lambda msg: print(msg, flush=True))
+    t.save(args.out)
+    print(f"wrote {len(t.entries)} classes to {args.out}")

@@ -136,3 +136,25 @@ def test_roofline_selector():
     assert tu["thread_mapped"] == tu["merge_path"]  # short rows: both at the same ceiling
     assert autotune.choose_by_roofline(uniform, 1000, calib) == "merge_path"  # ties go to merge path
     assert tu["nonzero_split"] > tu["merge_path"]
+
+
+def test_shipped_gb300_table():
+    """The table measured on a GB300 loads, names only schedules and launch shapes the library
+    has, and covers the standard workloads' classes (the stencil's winner is thread-mapped,
+    the power-law matrices' merge path)."""
+    from paper_2212_08964_gb300 import lbspmv
+
+    t = autotune.default_table()
+    assert t is not None and t.entries
+    for key, e in t.entries.items():
+        b = e["best"]
+        assert b["schedule"] in lbspmv.SCHEDULES
+        if b["schedule"] == "merge_path":
+            assert (b["threads"], b["items_per_thread"]) in lbspmv.MERGE_SHAPES
+        assert e["ms"] == min(c["ms"] for c in e["candidates"])
+    stencil = synth.workload("stencil7_160", 0.05)
+    full_stencil_class = "size24-mean5-skew0-lrb2-f32"
+    assert full_stencil_class in t.entries
+    assert t.lookup(full_stencil_class)["schedule"] == "thread_mapped"
+    assert autotune.shape_class(stencil.row_offsets).endswith("-f32")
+    assert t.lookup("size26-mean7-skew4-lrb2-f32")["schedule"] == "merge_path"
