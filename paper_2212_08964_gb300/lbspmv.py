@@ -519,11 +519,14 @@ class SpMV(torch.autograd.Function):
     gradient and the plan is merge-path, the forward saves x[col] of every nonzero (4 bytes per
     nonzero) and the backward streams them back instead of gathering x again; with both
     gradients wanted, one pass over the nonzeros forms dvalues and the scaled values for dx.
+    With ``deterministic=False`` dx comes from ``Plan.backward_scatter`` instead: one pass, no
+    CSC view, dx not bit-reproducible (within the same tolerance).
     """
 
     @staticmethod
-    def forward(ctx, values, x, plan: Plan, col_idx):
+    def forward(ctx, values, x, plan: Plan, col_idx, deterministic: bool = True):
         ctx.plan = plan
+        ctx.deterministic = deterministic
         xg = None
         if ctx.needs_input_grad[0] and plan.info()["schedule"] == "merge_path":
             xg = torch.empty(plan.nnz, dtype=torch.float32, device=x.device)
@@ -536,6 +539,14 @@ class SpMV(torch.autograd.Function):
         plan = ctx.plan
         g = g.contiguous().float()
         dvals = dx = None
+        if not ctx.deterministic and ctx.needs_input_grad[1]:
+            want_dv = ctx.needs_input_grad[0] and xg is not None
+            dx, dvals = plan.backward_scatter(col_idx, values.detach(), g, xg, want_dvalues=want_dv)
+            if ctx.needs_input_grad[0] and dvals is None:
+                dvals = plan.dvalues(col_idx, g, x.detach())
+            if dvals is not None and values.dtype != torch.float32:
+                dvals = dvals.to(values.dtype)
+            return dvals, dx, None, None, None
         if ctx.needs_input_grad[1] and not plan.has_transpose:
             plan.build_transpose(col_idx)
         if ctx.needs_input_grad[0] and ctx.needs_input_grad[1] and xg is not None:
@@ -547,12 +558,13 @@ class SpMV(torch.autograd.Function):
                 dx = plan.spmv_t(values.detach(), g)
         if dvals is not None and values.dtype != torch.float32:
             dvals = dvals.to(values.dtype)
-        return dvals, dx, None, None
+        return dvals, dx, None, None, None
 
 
-def spmv_autograd(plan: Plan, col_idx, values, x):
-    """Differentiable y = A x (see ``SpMV``)."""
-    return SpMV.apply(values, x, plan, col_idx)
+def spmv_autograd(plan: Plan, col_idx, values, x, deterministic: bool = True):
+    """Differentiable y = A x (see ``SpMV``); ``deterministic=False`` takes dx from the
+    one-pass scatter backward (no CSC view; not bit-reproducible)."""
+    return SpMV.apply(values, x, plan, col_idx, deterministic)
 
 
 def coo_row_offsets(row_idx, m: int, stream=None):

@@ -162,7 +162,10 @@ def test_two_pass_backward_unaligned_views(lb, orc):
 
 
 @pytest.mark.parametrize("sched", ["merge_path", "thread_mapped", "warp_mapped"])
-def test_autograd_function(lb, orc, sched):
+@pytest.mark.parametrize("deterministic", [True, False])
+def test_autograd_function(lb, orc, sched, deterministic):
+    """Both gradients through the autograd function; deterministic=False takes dx from the
+    scatter backward and builds no CSC view."""
     a = workload("powerlaw_4k")
     ro, ci, v = to_dev(a)
     plan = lb.Plan(ro, a.n, a.nnz, schedule=sched)
@@ -170,9 +173,10 @@ def test_autograd_function(lb, orc, sched):
     g = vec(a.m, 204)
     vt = v.clone().requires_grad_(True)
     xt = dev(x).requires_grad_(True)
-    y = lb.spmv_autograd(plan, ci, vt, xt)
+    y = lb.spmv_autograd(plan, ci, vt, xt, deterministic=deterministic)
     y.backward(dev(g))
     torch.cuda.synchronize()
+    assert plan.has_transpose == deterministic
     ref_dx = orc.spmv_t(a.row_offsets, a.col_idx, a.values, g, a.n)
     scale = orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n)
     check_bound(xt.grad.cpu().numpy(), ref_dx, scale, TOL32, "columns")
