@@ -100,51 +100,66 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
 // ------------------------------------------------------------------------------------------
 // Fixup ("Fix-up" procedure of Alg. alg:work-oriented): y[r] += the carries of row r.
 //
-// Carry rows are non-decreasing in tile order, so the carries of a row form one run.  A warp
-// takes each run start, finds the run's end with 32-way parallel probes, sums the run with
-// compensated per-lane sums and a fixed shuffle tree, and adds the total to y once: a fixed
-// order, so the result is deterministic, and no atomics.
+// Carry rows are non-decreasing in tile order, so the carries of a row form one run.  A thread
+// takes each carry; the first carry of a run of one (a row split over two tiles: most rows)
+// adds its value to y itself.  A longer run goes to the thread's warp, which finds the run's
+// end with 32-way parallel probes, sums the run with compensated per-lane sums and a fixed
+// shuffle tree, and adds the total to y once: a fixed order, so the result is deterministic,
+// and no atomics.
 __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *carry_row, const float *carry_val,
                                                     float *y) {
     const int lane = threadIdx.x & 31;
-    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
-    for (long long c = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; c < G; c += warps) {
-        const int r = __ldg(carry_row + c);
-        if (r >= m) continue;
-        if (c > 0 && __ldg(carry_row + c - 1) == r) continue;
-        // Galloping: lane l probes c + 2^l.
-        const long long probe = c + (1ll << lane);
-        const bool in_run = probe < G && __ldg(carry_row + probe) == r;
-        const unsigned run_mask = __ballot_sync(0xffffffffu, in_run);
-        const int L = __popc(run_mask);  // probes 1, 2, .., 2^(L-1) are inside the run
-        long long lo = L == 0 ? c : c + (1ll << (L - 1));
-        long long hi = c + (1ll << L);
-        if (hi > G) hi = G;
-        while (hi - lo > 1) {
-            const long long step = (hi - lo + 31) / 32;
-            const long long q = lo + (lane + 1) * step;
-            const bool in = q < hi && __ldg(carry_row + q) == r;
-            const int cnt = __popc(__ballot_sync(0xffffffffu, in));
-            const long long new_lo = lo + cnt * step;
-            long long new_hi = new_lo + step;
-            if (new_hi > hi) new_hi = hi;
-            lo = new_lo;
-            hi = new_hi;
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long c0 = static_cast<long long>(blockIdx.x) * blockDim.x; c0 < G; c0 += stride) {
+        // A thread per carry: the first carry of a row with no second one (most rows) adds its
+        // value itself; longer runs go to the warp below.
+        const long long c = c0 + threadIdx.x;
+        int r = m;
+        bool head = false, single = false;
+        if (c < G) {
+            r = __ldg(carry_row + c);
+            head = r < m && (c == 0 || __ldg(carry_row + c - 1) != r);
+            single = head && (c + 1 >= G || __ldg(carry_row + c + 1) != r);
+            if (single) y[r] += __ldg(carry_val + c);
         }
-        const long long end = hi;  // carries [c, end) belong to row r
-        float s = 0.f, comp = 0.f;
-        for (long long q = c + lane; q < end; q += 32) kbn_add(s, comp, __ldg(carry_val + q));
-        float v = s + comp;
+        for (unsigned todo = __ballot_sync(0xffffffffu, head && !single); todo; todo &= todo - 1) {
+            const int src = __ffs(todo) - 1;
+            const long long cs = __shfl_sync(0xffffffffu, c, src);
+            const int rs = __shfl_sync(0xffffffffu, r, src);
+            // Galloping: lane l probes cs + 2^l.
+            const long long probe = cs + (1ll << lane);
+            const bool in_run = probe < G && __ldg(carry_row + probe) == rs;
+            const unsigned run_mask = __ballot_sync(0xffffffffu, in_run);
+            const int L = __popc(run_mask);  // probes 1, 2, .., 2^(L-1) are inside the run
+            long long lo = L == 0 ? cs : cs + (1ll << (L - 1));
+            long long hi = cs + (1ll << L);
+            if (hi > G) hi = G;
+            while (hi - lo > 1) {
+                const long long step = (hi - lo + 31) / 32;
+                const long long q = lo + (lane + 1) * step;
+                const bool in = q < hi && __ldg(carry_row + q) == rs;
+                const int cnt = __popc(__ballot_sync(0xffffffffu, in));
+                const long long new_lo = lo + cnt * step;
+                long long new_hi = new_lo + step;
+                if (new_hi > hi) new_hi = hi;
+                lo = new_lo;
+                hi = new_hi;
+            }
+            const long long end = hi;  // carries [cs, end) belong to row rs
+            float sum = 0.f, comp = 0.f;
+            for (long long q = cs + lane; q < end; q += 32) kbn_add(sum, comp, __ldg(carry_val + q));
+            float v = sum + comp;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) y[r] += v;
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) y[rs] += v;
+        }
     }
 }
 
 cudaError_t launch_fixup(int num_tiles, int num_rows, const int *carry_row, const float *carry_val, float *y,
                          cudaStream_t stream) {
     if (num_tiles <= 0) return cudaSuccess;
-    long long blocks = (static_cast<long long>(num_tiles) + 7) / 8;
+    long long blocks = (static_cast<long long>(num_tiles) + 255) / 256;  // a thread per carry
     const long long cap = static_cast<long long>(current_sm_count()) * 8;
     if (blocks > cap) blocks = cap;
     fixup_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(num_tiles, num_rows, carry_row, carry_val, y);
