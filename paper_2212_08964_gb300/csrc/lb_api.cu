@@ -289,7 +289,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
         MergeArgs a{};
         a.num_tiles = G;
         a.num_rows = m;
-    a.num_atoms = nnz;
+        a.num_atoms = nnz;
         a.tile_row = tile_row;
         a.tile_nz = tile_nz;
         a.row_end = row_offsets + 1;

@@ -28,59 +28,75 @@ int current_sm_count() {
 // (K_{-1} = -1, K_m = W).  Instead of one binary search per boundary, every row r computes
 // the boundaries c with d_c = min(c T, W) in that interval and writes (r, d_c - r) for them:
 // one coalesced pass over the offsets, the same result bit for bit.  A warp shares the
-// writes of its 32 rows, so a row spanning many tiles does not serialize one thread.
+// writes of its 32 rows, so a row spanning many tiles does not serialize one thread; each warp
+// step loads four chunks of 32 rows' offsets before working on them.
 __global__ void __launch_bounds__(256) partition_kernel(int m, long long W, int T, long long G, const int *offsets,
                                                         int *tile_row, int *tile_nz) {
+    constexpr int U = 4;  // 32-row chunks per warp step, their offsets loaded together
     const int lane = threadIdx.x & 31;
+    const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
-    for (long long base = ((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; base <= m;
-         base += warps * 32) {
-        const long long r = base + lane;
-        long long c_lo = 0, n_c = 0;
-        // Each lane loads offsets[r+1]; offsets[r] comes from the lane below (lane 0 loads it).
-        const int end_off = (r < m) ? __ldg(offsets + r + 1) : 0;
-        int start_off = __shfl_up_sync(0xffffffffu, end_off, 1);
-        if (lane == 0 && r > 0 && r <= m) start_off = __ldg(offsets + r);
-        if (r <= m) {
-            // Merge positions fit 32 bits (m + nnz < 2^32): 32-bit division, not 64-bit.
-            const long long k_prev = (r == 0) ? -1 : (r - 1) + static_cast<long long>(start_off);
-            const long long k_cur = (r == m) ? W : r + static_cast<long long>(end_off);
-            const unsigned Tu = static_cast<unsigned>(T);
-            c_lo = k_prev + 1 > 0 ? (static_cast<unsigned>(k_prev) + Tu) / Tu : 0;
-            long long c_hi = (r == m) ? G : static_cast<unsigned>(k_cur) / Tu;
-            if (c_hi > G) c_hi = G;  // only malformed offsets get here; keep writes in [0, G]
-            n_c = c_hi >= c_lo ? c_hi - c_lo + 1 : 0;
-        }
-        // Exclusive prefix of the per-lane boundary counts.
-        long long incl = n_c;
+    for (long long base0 = warp * 32 * U; base0 <= m; base0 += warps * 32 * U) {
+        // Each lane loads offsets[r+1] of its row in every chunk; offsets[r] comes from the lane
+        // below (lane 0 loads it).
+        int end_offs[U], lane0_start[U];
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += t;
+        for (int u = 0; u < U; ++u) {
+            const long long r = base0 + 32 * u + lane;
+            end_offs[u] = (r < m) ? __ldg(offsets + r + 1) : 0;
+            lane0_start[u] = (lane == 0 && r > 0 && r <= m) ? __ldg(offsets + r) : 0;
         }
-        const long long total = __shfl_sync(0xffffffffu, incl, 31);
-        const long long excl = incl - n_c;
-        for (long long q0 = 0; q0 < total; q0 += 32) {  // warp-uniform trip count
-            const long long q = q0 + lane;
-            // Owner: the last lane whose exclusive prefix is <= q.
-            int lo = 0, hi = 31;
 #pragma unroll
-            for (int step = 0; step < 5; ++step) {
-                const int mid = (lo + hi + 1) >> 1;
-                const long long e_mid = __shfl_sync(0xffffffffu, excl, mid);
-                if (e_mid <= q)
-                    lo = mid;
-                else
-                    hi = mid - 1;
+        for (int u = 0; u < U; ++u) {
+            const long long base = base0 + 32 * u;
+            if (base > m) break;  // warp-uniform
+            const long long r = base + lane;
+            long long c_lo = 0, n_c = 0;
+            const int end_off = end_offs[u];
+            int start_off = __shfl_up_sync(0xffffffffu, end_off, 1);
+            if (lane == 0) start_off = lane0_start[u];
+            if (r <= m) {
+                // Merge positions fit 32 bits (m + nnz < 2^32): 32-bit division, not 64-bit.
+                const long long k_prev = (r == 0) ? -1 : (r - 1) + static_cast<long long>(start_off);
+                const long long k_cur = (r == m) ? W : r + static_cast<long long>(end_off);
+                const unsigned Tu = static_cast<unsigned>(T);
+                c_lo = k_prev + 1 > 0 ? (static_cast<unsigned>(k_prev) + Tu) / Tu : 0;
+                long long c_hi = (r == m) ? G : static_cast<unsigned>(k_cur) / Tu;
+                if (c_hi > G) c_hi = G;  // only malformed offsets get here; keep writes in [0, G]
+                n_c = c_hi >= c_lo ? c_hi - c_lo + 1 : 0;
             }
-            const long long e_own = __shfl_sync(0xffffffffu, excl, lo);
-            const long long c_own = __shfl_sync(0xffffffffu, c_lo, lo);
-            if (q >= total) continue;
-            const long long c = c_own + (q - e_own);
-            const long long row = base + lo;
-            const long long d = c * T < W ? c * T : W;
-            tile_row[c] = static_cast<int>(row);
-            tile_nz[c] = static_cast<int>(d - row);
+            if (__ballot_sync(0xffffffffu, n_c > 0) == 0u) continue;  // no boundary in these 32 rows (most)
+            // Exclusive prefix of the per-lane boundary counts.
+            long long incl = n_c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            const long long total = __shfl_sync(0xffffffffu, incl, 31);
+            const long long excl = incl - n_c;
+            for (long long q0 = 0; q0 < total; q0 += 32) {  // warp-uniform trip count
+                const long long q = q0 + lane;
+                // Owner: the last lane whose exclusive prefix is <= q.
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    const long long e_mid = __shfl_sync(0xffffffffu, excl, mid);
+                    if (e_mid <= q)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const long long e_own = __shfl_sync(0xffffffffu, excl, lo);
+                const long long c_own = __shfl_sync(0xffffffffu, c_lo, lo);
+                if (q >= total) continue;
+                const long long c = c_own + (q - e_own);
+                const long long row = base + lo;
+                const long long d = c * T < W ? c * T : W;
+                tile_row[c] = static_cast<int>(row);
+                tile_nz[c] = static_cast<int>(d - row);
+            }
         }
     }
 }
@@ -89,9 +105,11 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
                              cudaStream_t stream) {
     const long long W = static_cast<long long>(m) + nnz;
     const long long G = (W + tile_items - 1) / tile_items;
-    const long long threads_needed = (static_cast<long long>(m) + 1 + 31) / 32 * 32;
-    long long blocks = (threads_needed + 255) / 256;  // one warp per 32 rows: latency, not bandwidth, is the limit
-    if (blocks > (1ll << 30)) blocks = 1ll << 30;
+    // A warp per four 32-row chunks (their loads in flight together), grid-strided beyond one
+    // wave of 16 blocks per SM.
+    long long blocks = (static_cast<long long>(m) + 1 + 1023) / 1024;
+    const long long cap = static_cast<long long>(current_sm_count()) * 16;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     partition_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(m, W, tile_items, G, offsets, tile_row, tile_nz);
     return cudaGetLastError();
