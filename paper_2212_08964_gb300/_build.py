@@ -23,6 +23,7 @@ SOURCES = [
     "lb_merge_bf16.cu",
     "lb_merge_f16.cu",
     "lb_transpose.cu",
+    "lb_backward.cu",
     "lb_mapped.cu",
     "lb_partition.cu",
     "lb_api.cu",

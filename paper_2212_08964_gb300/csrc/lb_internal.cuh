@@ -208,6 +208,9 @@ cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_ite
                                 const int *tile_nz, const int *row_end, const float *g, const void *values,
                                 const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream);
 
+// rowid[k] = the row of nonzero k, over the forward partition.
+cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
+                                const int *row_end, int *rowid, cudaStream_t stream);
 // The same pass adding v[k] * g[row(k)] into dx[col_idx[k]] with float reductions (dx zeroed
 // by the caller; not bit-reproducible), and dv[k] = g[row(k)] * xg[k] when dv is given.
 cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
