@@ -459,26 +459,35 @@ __device__ __forceinline__ void gather_issue(const MergeArgs &a, const unsigned 
     }
 }
 
-// The forward product's saved gathers: xg[k] = x[col_idx[k]] for gather thread g's nonzeros
-// (streaming stores; 16-byte vector stores when the thread's slots are all nonzeros of the
-// tile and aligned).  The values gradient reads them back instead of gathering x again.
+// The forward product's saved gathers, xg[k] = x[col_idx[k]], written coalesced.  A warp's
+// gathered values first replace its own staged column indices: its slots holding the tile's
+// nonzeros ([lead, lead + nk), the staged indices themselves), which nothing reads any more.
+// The warp then reads them back lane by lane, so each store instruction writes 32 consecutive
+// nonzeros (streaming stores).  Runs before the warp releases the stage.
 template <int IPT>
-__device__ __forceinline__ void save_gathered(float *xg, const StageHdr &h, int g, const float (&xv)[IPT]) {
-    const int nk = h.k1 - h.k0;
-    const int item0 = g * IPT - tile_lead(h);
-    if (item0 + IPT <= 0 || item0 >= nk) return;
-    if (item0 >= 0 && item0 + IPT <= nk) {
-        float *dst = xg + h.k0 + item0;
-        if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+__device__ __forceinline__ void save_gathered(float *xg, unsigned char *stage, const StageHdr &h, int g, int gwarp,
+                                              const float (&xv)[IPT]) {
+    const int lane = threadIdx.x & 31;
+    const int nk = h.k1 - h.k0, lead = tile_lead(h);
+    float *slots = reinterpret_cast<float *>(stage + h.idx_first - lead * 4);  // slot 0, 16-byte aligned
+    const int slot0 = g * IPT;
+    if (slot0 >= lead && slot0 + IPT <= lead + nk) {
 #pragma unroll
-            for (int q = 0; q < IPT; q += 4)
-                __stcs(reinterpret_cast<float4 *>(dst + q), make_float4(xv[q], xv[q + 1], xv[q + 2], xv[q + 3]));
-            return;
-        }
+        for (int q = 0; q < IPT; q += 4)
+            *reinterpret_cast<float4 *>(slots + slot0 + q) = make_float4(xv[q], xv[q + 1], xv[q + 2], xv[q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
+            if (slot0 + q >= lead && slot0 + q < lead + nk) slots[slot0 + q] = xv[q];
     }
+    __syncwarp();
+    const int S0 = gwarp * 32 * IPT;
+    float *dst = xg + h.k0 - lead;  // slot s holds nonzero k0 - lead + s
 #pragma unroll
-    for (int q = 0; q < IPT; ++q)
-        if (item0 + q >= 0 && item0 + q < nk) __stcs(xg + h.k0 + item0 + q, xv[q]);
+    for (int q = 0; q < IPT; ++q) {
+        const int sl = S0 + q * 32 + lane;
+        if (sl >= lead && sl < lead + nk) __stcs(dst + sl, slots[sl]);
+    }
 }
 
 // Row-start bits of one gather warp's 32 * IPT slots of a tile, built by the warp alone from
@@ -625,11 +634,17 @@ __global__ void __launch_bounds__(MergeShape<GW, IPT, static_cast<int>(MergeTrai
                 for (int q = 0; q < IPT; ++q) vv[q] = xv[q] = 0.f;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars->gdone[s]);  // the stage is no longer read here
+            // The stage is no longer read here, unless the gathers are saved through it.
+            const bool save = MODE == kPlain && a.xg != nullptr && h.ok;
+            if (!save && lane == 0) mbar_arrive(&bars->gdone[s]);
             float v[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) v[q] = vv[q] * xv[q];
-            if (MODE == kPlain && a.xg != nullptr && h.ok) save_gathered<IPT>(a.xg, h, g, xv);
+            if (save) {
+                save_gathered<IPT>(a.xg, stages + s * Sh::STAGE, h, g, warp, xv);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars->gdone[s]);
+            }
 #pragma unroll
             for (int q = 1; q < IPT; ++q)
                 if (!((flags >> q) & 1u)) v[q] += v[q - 1];
