@@ -7,7 +7,8 @@
 // transposed SpMV sums every column in a fixed order.  It is built once per sparsity
 // structure with a least-significant-digit radix sort of (column, CSR index) pairs: 8-bit
 // digits, per-block digit counts, one exclusive scan over (digit, block), then a scatter in
-// which every element's rank among equal digits of its block comes from warp match masks.
+// which every element's rank among equal digits of its block comes from warp match masks; a
+// block orders its tile by digit in shared memory and writes it out digit run by digit run.
 // Every step is a pure function of its input, so the plan is bit-exact and deterministic.
 #include <cstdlib>
 #include <cstring>
