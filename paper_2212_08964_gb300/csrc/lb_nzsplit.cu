@@ -9,11 +9,12 @@
 // is this schedule's cost on matrices with many empty rows.
 //
 // Per tile (T = 2048 nonzeros): the rows starting inside the tile add 1 to a per-slot count,
-// and a block scan gives each nonzero's row; each thread walks its 8 consecutive nonzeros,
-// writes the rows that start and end among them, and hands its first and last partial row to
-// shared memory; the range where a row first appears sums it forward across ranges.  The
-// tile's first and last rows, which may continue in the neighbouring tiles, go out as two
-// carries, and the fixup adds each row's carries in tile order: deterministic, no atomics on y.
+// and a block scan gives each nonzero's row; each thread walks its 8 consecutive nonzeros and
+// writes the rows that start and end among them.  Rows spanning threads are summed by a
+// segmented scan of the threads' last partial rows, in thread order, and written where they
+// end.  The tile's first and last rows, which may continue in the neighbouring tiles, go out
+// as two carries, and the fixup adds each row's carries in tile order: deterministic, no
+// atomics on y.
 #include <cstring>
 
 #include "lb_internal.cuh"
@@ -81,8 +82,11 @@ __global__ void __launch_bounds__(kNzThreads) nzsplit_kernel(int G, int m, int n
     constexpr int WARPS = kNzThreads / 32;
     __shared__ __align__(16) int cnt[T];
     __shared__ int wsum[WARPS];
-    __shared__ int p_row[2][kNzThreads];
-    __shared__ float p_val[2][kNzThreads];
+    __shared__ int s_tail[kNzThreads];    // each thread's last row (-1: no nonzeros)
+    __shared__ int s_first[kNzThreads];   // each thread's first row
+    __shared__ float s_tval[kNzThreads];  // scanned tail values
+    __shared__ float w_val[WARPS];
+    __shared__ int w_seg[WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(ci) & 15u) == 0 && (reinterpret_cast<uintptr_t>(values) & 15u) == 0;
     for (int i = tid; i < T; i += kNzThreads) cnt[i] = 0;
@@ -163,46 +167,59 @@ __global__ void __launch_bounds__(kNzThreads) nzsplit_kernel(int G, int m, int n
             }
             acc += prod[q];
         }
-        if (first < 0) {
-            p_row[0][tid] = cur;
-            p_val[0][tid] = acc;
-            p_row[1][tid] = -1;
-        } else {
-            p_row[0][tid] = first;
-            p_val[0][tid] = facc;
-            p_row[1][tid] = cur;
-            p_val[1][tid] = acc;
-        }
+        // This thread's partial rows: its first row (f, a), and when another row follows, its
+        // last row (l, b).  Rows spanning threads are summed by a segmented scan over the
+        // threads in order; each row's total is written where its last segment lies.
+        const bool active = j0 < nk;
+        const bool has2 = first >= 0;
+        const int f = has2 ? first : cur;
+        const float a = has2 ? facc : acc;
+        const int L = active ? cur : -1;  // the thread's tail row
         if (tid == 0) {  // the tile's two carries start empty
             carry_row[2 * tile] = r_first;
             carry_val[2 * tile] = 0.f;
             carry_row[2 * tile + 1] = r_last;
             carry_val[2 * tile + 1] = 0.f;
         }
+        s_tail[tid] = L;
         __syncthreads();
-        // Heads: the range where a row first appears sums it forward through the ranges.
+        const int prevL = tid > 0 ? s_tail[tid - 1] : -1;
+        const bool cont = active && !has2 && f == prevL;  // the tail continues the previous thread's
+        // Segmented inclusive scan of the tail values, restarting where a tail does not continue.
+        float tv = active ? acc : 0.f;
+        bool seg = !cont;
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            const int R = p_row[w][tid];
-            if (R < 0) continue;
-            if (w == 0 && tid > 0) {
-                const int prev = p_row[1][tid - 1] >= 0 ? p_row[1][tid - 1] : p_row[0][tid - 1];
-                if (prev == R) continue;
-            }
-            float sum = p_val[w][tid];
-            if (w == 1 || p_row[1][tid] < 0) {
-                for (int t2 = tid + 1; t2 < kNzThreads; ++t2) {
-                    if (p_row[0][t2] != R) break;
-                    sum += p_val[0][t2];
-                    if (p_row[1][t2] >= 0) break;
-                }
-            }
-            if (R == r_first)
-                carry_val[2 * tile] = sum;  // may continue from the tile before
-            else if (R == r_last)
-                carry_val[2 * tile + 1] = sum;  // may continue into the tile after
-            else
-                y[R] = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            const float v_up = __shfl_up_sync(0xffffffffu, tv, off);
+            const int s_up = __shfl_up_sync(0xffffffffu, static_cast<int>(seg), off);
+            if (lane >= off && !seg) tv += v_up;
+            if (lane >= off) seg = seg || s_up;
+        }
+        if (lane == 31) {
+            w_val[warp] = tv;
+            w_seg[warp] = seg ? 1 : 0;
+        }
+        __syncthreads();
+        if (!seg) {  // no restart in this warp up to here: add the carry of the warps before
+            float c = 0.f;
+            for (int w = 0; w < warp; ++w) c = w_seg[w] ? w_val[w] : c + w_val[w];
+            tv += c;
+        }
+        s_tval[tid] = tv;
+        s_first[tid] = active ? f : -1;
+        __syncthreads();
+        if (active) {
+            auto put = [&](int R, float v) {
+                if (R == r_first)
+                    carry_val[2 * tile] = v;  // may continue from the tile before
+                else if (R == r_last)
+                    carry_val[2 * tile + 1] = v;  // may continue into the tile after
+                else
+                    y[R] = v;
+            };
+            if (has2) put(f, a + (tid > 0 && prevL == f ? s_tval[tid - 1] : 0.f));  // the first row ends here
+            const bool tail_ends = tid + 1 == kNzThreads || s_first[tid + 1] != L;
+            if (tail_ends) put(L, tv);
         }
         __syncthreads();
     }
