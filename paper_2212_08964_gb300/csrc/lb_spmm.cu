@@ -154,6 +154,44 @@ __global__ void __launch_bounds__(THREADS) spmm_kernel(int G, int m, int kc, int
                 if (4 * q + 2 < kc) cv[2] = 0.f;
                 if (4 * q + 3 < kc) cv[3] = 0.f;
             }
+            if (nr == 0) {
+                // No row ends in the tile: all its nonzeros belong to the open row.  Each range
+                // sums its products, a tree over the ranges (fixed order) adds them up, and the
+                // total is the tile's carry.
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (active) {
+                    constexpr int U = 8;
+                    for (int j0 = jb; j0 < je; j0 += U) {
+                        float4 b[U];
+                        float vl[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int j = j0 + u;
+                            const bool in = j < je;
+                            vl[u] = in ? s_val[j] : 0.f;
+                            b[u] = in ? load_b4<VEC>(B, s_col[j], kc, q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) fma4(acc, vl[u], b[u]);
+                    }
+                }
+                p_acc[0][tid] = acc;
+                __syncthreads();
+                for (int half = ng >> 1; half > 0; half >>= 1) {  // ng is a power of two
+                    if (g < half) p_acc[0][tid] = add4(p_acc[0][tid], p_acc[0][tid + half * nq]);
+                    __syncthreads();
+                }
+                if (active && g == 0) {
+                    const float4 sum = p_acc[0][tid];
+                    float *cv = carry_val + static_cast<long long>(tile) * kc + 4 * q;
+                    if (4 * q < kc) cv[0] = sum.x;
+                    if (4 * q + 1 < kc) cv[1] = sum.y;
+                    if (4 * q + 2 < kc) cv[2] = sum.z;
+                    if (4 * q + 3 < kc) cv[3] = sum.w;
+                }
+                __syncthreads();
+                continue;
+            }
             // Walk this range's nonzeros in order.
             int cur = -1, first_row = -1;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), first_acc = acc;
