@@ -44,7 +44,7 @@ typedef enum {
     LB_OK = 0,
     LB_ERR_INVALID_ARG = -1, /* bad size, null pointer, unknown enum, plan of the wrong kind */
     LB_ERR_BAD_MATRIX = -2,  /* malformed matrix contents (found by a check or a kernel) */
-    LB_ERR_UNSUPPORTED = -3, /* valid request this build does not implement */
+    LB_ERR_UNSUPPORTED = -3, /* valid request this library does not implement */
     LB_ERR_NO_MEMORY = -4,   /* a plan or workspace allocation failed */
     LB_ERR_CUDA = -5,        /* a CUDA runtime call failed */
     LB_ERR_TIMEOUT = -6,     /* a kernel gave up on a bounded wait (device error word) */
@@ -303,7 +303,7 @@ void lb_batched_plan_destroy(lb_batched_plan *p);
 /*
  * Autotuner timing core.  The dissertation chooses a schedule by a fixed size rule (Ch.4 Sec.
  * "Improved Performance Response"); lb_tune measures instead.  Every candidate schedule and
- * launch shape this build implements (merge-path at each shape, thread-mapped, warp-mapped,
+ * launch shape this library implements (merge-path at each shape, thread-mapped, warp-mapped,
  * group-mapped with 4, 8 and 16 lanes, block-mapped with 128 and 256 threads) builds a plan
  * and runs y = A x `reps` times on `stream`, timed by CUDA events after one untimed call.
  * Results (schedule, resolved tuning, mean milliseconds) are written sorted fastest first,

@@ -226,7 +226,7 @@ const char *lb_status_string(lb_status s) {
         case LB_ERR_BAD_MATRIX:
             return "LB_ERR_BAD_MATRIX: malformed matrix";
         case LB_ERR_UNSUPPORTED:
-            return "LB_ERR_UNSUPPORTED: not supported by this build";
+            return "LB_ERR_UNSUPPORTED: not supported by this library";
         case LB_ERR_NO_MEMORY:
             return "LB_ERR_NO_MEMORY: device allocation failed";
         case LB_ERR_CUDA:
