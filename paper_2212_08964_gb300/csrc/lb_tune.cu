@@ -18,7 +18,7 @@ struct Candidate {
     lb_tuning t;
 };
 
-// Every schedule and launch shape this build implements.
+// Every schedule and launch shape this library implements.
 std::vector<Candidate> all_candidates() {
     std::vector<Candidate> c;
     const int merge[][2] = {{256, 8}, {128, 16}, {256, 16}, {384, 8}, {512, 8}};
