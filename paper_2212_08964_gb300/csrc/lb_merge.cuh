@@ -23,7 +23,9 @@
 //   * gather warps (GW) read their IPT consecutive slots of a staged tile with vector loads,
 //     issue the x gathers, build their slots' row-start bits from the staged row ends while
 //     the gathers are in flight, then scan their own products (restarting at row starts)
-//     into one of two product buffers, with one aggregate per thread;
+//     into one of two product buffers, with one aggregate per thread.  When the forward saves
+//     its gathers for the values gradient, a warp writes them over its own staged indices and
+//     stores them 32 consecutive per instruction before it releases the stage;
 //   * scan warps (SW): the first scans the gather threads' aggregates into the carry into
 //     each thread's first row; then all of them read each finished row's sum at its last
 //     nonzero, write y with coalesced stores, and write the open row's partial sum as the
@@ -47,7 +49,7 @@
 namespace lb {
 
 // Shape of one CTA: GW gather warps with IPT slots per thread; a tile holds T slots.  SV is
-// the size of the third staged array (values, or CSR positions for the transposed product);
+// the size of a staged value (0 for the gather-sum, which stages only row ends and positions);
 // NS is the number of shared-memory stages, NB the number of product buffers, RB the register
 // budget per thread that sets the resident CTAs per SM.
 template <int GW, int IPT, int SV, int NS, int NB, int RB>
