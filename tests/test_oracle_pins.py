@@ -7,7 +7,9 @@
 * library routines: numpy dense matvec and scipy.sparse (SpMV, transpose, A^T g);
 * closed forms and special cases: identity, diagonal, permutation, integer-valued exact sums,
   the column-sum invariant sum(y) = (1^T A) x;
-* central finite differences of the quadratic loss L = 1/2||Ax - t||^2, exact up to rounding.
+* central finite differences of the quadratic loss L = 1/2||Ax - t||^2, exact up to rounding;
+* the tolerance scales |A| |x| and |A|^T |g| (and their batched form) against scipy;
+* SpMM against dense and sparse products, SSSP against scipy's Dijkstra and a worked graph.
 """
 import itertools
 
@@ -295,6 +297,28 @@ def test_batched_spmv_vs_scipy_block_diag(orc):
     mats = [_scipy(b.matrix(i)) for i in range(b.count)]
     ref = sp.block_diag(mats, format="csr") @ x.astype(np.float64)
     np.testing.assert_allclose(orc.batched_spmv(b, x), ref, atol=1e-12, rtol=0)
+
+
+def test_tolerance_scales_vs_scipy(orc):
+    """The scales every tolerance is measured in: sum_j |a_ij| |x_j| per row (|A| |x|),
+    sum_i |a_ij| |g_i| per column (|A|^T |g|), their batched form over the block-diagonal
+    matrix, and the tile count ceil((m + nnz) / T)."""
+    rng = np.random.default_rng(31)
+    a = synth.csr_from_row_lengths(rng, 120, rng.integers(0, 25, 150))
+    x = rng.standard_normal(a.n)
+    g = rng.standard_normal(a.m)
+    A = abs(_scipy(a))
+    np.testing.assert_allclose(orc.row_absdot(a.row_offsets, a.col_idx, a.values, x), A @ np.abs(x),
+                               rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(orc.col_absdot(a.row_offsets, a.col_idx, a.values, g, a.n), A.T @ np.abs(g),
+                               rtol=1e-13, atol=1e-13)
+    b = synth.batched_powerlaw(12, 8, 200, 2500, 1.5, seed=23)
+    xb = rng.standard_normal(int(b.ns.sum()))
+    mats = [abs(_scipy(b.matrix(i))) for i in range(b.count)]
+    np.testing.assert_allclose(orc.batched_row_absdot(b, xb), sp.block_diag(mats, format="csr") @ np.abs(xb),
+                               rtol=1e-13, atol=1e-13)
+    for m, nnz, T in ((0, 0, 5), (1, 0, 5), (7, 3, 5), (4096, 64080, 2040), (10, 10, 1)):
+        assert orc.num_tiles(m, nnz, T) == -(-(m + nnz) // T)
 
 
 @pytest.mark.parametrize("name", ["powerlaw_4k"])
