@@ -107,20 +107,22 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
  * Schedule: always merge-path with the (256, 8) launch shape (tiles of
  * LB_SPMV_STATIC_TILE_ITEMS work items), whatever the matrix size.
  * Workspace: a file-scope __device__ array inside the library, one per device, holding the
- * partition and carry arrays of at most LB_SPMV_STATIC_MAX_TILES tiles (about 1 MiB).  So
+ * partition and carry arrays of at most LB_SPMV_STATIC_MAX_TILES tiles (8 MiB).  So
  * m + nnz must be at most LB_SPMV_STATIC_MAX_TILES * LB_SPMV_STATIC_TILE_ITEMS
- * (133,693,440); larger requests return LB_ERR_TOO_LARGE before any GPU work.
+ * (130,023,424); larger requests return LB_ERR_TOO_LARGE before any GPU work.
  * Set-up: the FIRST call on each device (with that device current) looks up the array's
- * device address (cudaGetSymbolAddress), caches it, and sets the merge-path kernel's
- * shared-memory limit; make that first call before any stream capture.  Later calls only enqueue two small memsets (the carry arrays are cleared
- * every call) and the partition, merge-path and fixup kernels on `stream`.
+ * device address (cudaGetSymbolAddress), caches it, and does the merge-path kernel's
+ * host-side set-up (shared-memory carveout, occupancy) for all three value types; make that
+ * first call before any stream capture.  Later calls only enqueue one small memset (the
+ * carry rows are filled with -1 every call) and the partition, merge-path and fixup kernels
+ * on `stream`.
  * Concurrency: every call on one device shares the one workspace, so calls that overlap in
  * time (on different streams, or from several host threads without stream ordering between
  * them) RACE and give wrong results.  Calls ordered on one stream are safe.
  * Arguments, results and other errors are as for lb_spmv.
  */
-#define LB_SPMV_STATIC_MAX_TILES 65536
-#define LB_SPMV_STATIC_TILE_ITEMS 2040
+#define LB_SPMV_STATIC_MAX_TILES 524288
+#define LB_SPMV_STATIC_TILE_ITEMS 248
 lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offsets, const int *col_idx,
                          const void *values, lb_dtype vdt, const float *x, float *y,
                          cudaStream_t stream);
@@ -149,16 +151,37 @@ int lb_num_tiles(int m, int nnz, int tile_items);
 lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_schedule s,
                          const lb_tuning *t, cudaStream_t stream, lb_plan **out);
 
-/* Resolved schedule and launch shape of a plan; any output pointer may be NULL. */
+/*
+ * Resolved schedule and launch shape of a plan; any output pointer may be NULL.  num_tiles and
+ * tile_items describe the LB_TILES_ROWS tile set (below).
+ */
 lb_status lb_plan_info(const lb_plan *p, lb_schedule *s, lb_tuning *t, int *num_tiles,
                        int *tile_items);
 
 /*
- * Copy a plan's merge-path partition to HOST arrays of num_tiles + 1 ints (synchronizes
- * the device).  transposed = 0: the forward (CSR) partition; 1: the CSC partition built by
- * lb_plan_build_transpose.  With tile_row == NULL only *num_tiles is written.
+ * A plan's tile sets, each a merge-path partition (Alg. alg:work-oriented) of its own tile
+ * size:
+ *   LB_TILES_ROWS        tiles of threads * items_per_thread - 8 work items, walked by the
+ *                        block-level passes over the forward partition (dvalues gathering x,
+ *                        the transpose and SpMM); every plan;
+ *   LB_TILES_TRANSPOSED  warp tiles (248 work items) of the transposed product's merge path
+ *                        over the CSC view; after lb_plan_build_transpose;
+ *   LB_TILES_MERGE       warp tiles (32 * items_per_thread - 8 work items; 248 for schedules
+ *                        other than merge-path) of the merge-path forward and of the CSR-order
+ *                        backward pass; every plan with m > 0.
+ * lb_plan_tiles gives a set's tile count and size; LB_ERR_INVALID_ARG for a set the plan
+ * does not hold.
  */
-lb_status lb_plan_partition(const lb_plan *p, int transposed, int *tile_row, int *tile_nz,
+#define LB_TILES_ROWS 0
+#define LB_TILES_TRANSPOSED 1
+#define LB_TILES_MERGE 2
+lb_status lb_plan_tiles(const lb_plan *p, int which, int *num_tiles, int *tile_items);
+
+/*
+ * Copy one of a plan's tile sets (`which`, above) to HOST arrays of num_tiles + 1 ints
+ * (synchronizes the device).  With tile_row == NULL only *num_tiles is written.
+ */
+lb_status lb_plan_partition(const lb_plan *p, int which, int *tile_row, int *tile_nz,
                             int *num_tiles);
 
 /* y = A x with a plan (no allocation, no synchronization; CUDA-graph capturable). */

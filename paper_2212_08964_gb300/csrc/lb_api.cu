@@ -116,9 +116,14 @@ bool sizes_ok(int m, int n, int nnz) {
     return true;
 }
 
-// Work items per merge-path tile: threads * items_per_thread slots, less 8 kept for the
-// lead of a tile's first nonzero past a 16-byte boundary.
-int merge_tile_items(int threads, int ipt) { return threads * ipt - 8; }
+// Work items per tile of the block-level passes over the forward partition (the CSR-order
+// backward pass, dvalues, the transpose and SpMM): threads * items_per_thread slots, less 8.
+int cta_tile_items(int threads, int ipt) { return threads * ipt - 8; }
+
+size_t value_bytes(lb_dtype d) { return d == LB_F32 ? 4 : 2; }
+
+// Pointers must be aligned to their element type (the kernels use vector accesses).
+bool aligned(const void *p, size_t bytes) { return (reinterpret_cast<uintptr_t>(p) & (bytes - 1)) == 0; }
 
 int num_tiles_of(long long m, long long nnz, int tile_items) {
     const long long W = m + nnz;
@@ -146,8 +151,13 @@ struct lb_plan {
     int *ro = nullptr;
     int *tile_row = nullptr, *tile_nz = nullptr, *carry_row = nullptr;
     float *carry_val = nullptr;
+    // Warp tiles (merge_tile_items(items_per_thread) items): the merge-path forward and the
+    // per-nonzero passes of the backward.
+    int wG = 0, w_tile_items = 0;
+    int *w_tile_row = nullptr, *w_tile_nz = nullptr, *w_carry_row = nullptr;
+    float *w_carry_val = nullptr;
     bool has_t = false;
-    int Gt = 0;
+    int Gt = 0, t_tile_items = 0;  // warp tiles of the transposed (gather-sum) product
     int *co = nullptr, *ri = nullptr, *perm = nullptr;
     int *t_tile_row = nullptr, *t_tile_nz = nullptr, *t_carry_row = nullptr;
     float *t_carry_val = nullptr;
@@ -204,10 +214,11 @@ static void free_plan_arrays(lb_plan *p) {
     p->mm_carry_row = nullptr;
     p->mm_carry_val = nullptr;
     p->mm_cols = 0;
-    int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row};
+    int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row, p->w_tile_row, p->w_tile_nz, p->w_carry_row};
     for (int *q : ints)
         if (q) cudaFree(q);
     if (p->carry_val) cudaFree(p->carry_val);
+    if (p->w_carry_val) cudaFree(p->w_carry_val);
 }
 
 static bool on_device(int dev) {
@@ -270,9 +281,11 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
     lb_tuning t;
     if (!resolve(m, n, nnz, LB_SCHED_AUTO, nullptr, &s, &t)) return LB_ERR_INVALID_ARG;
     if (s != LB_SCHED_MERGE_PATH) return from_cuda(launch_mapped(s, t, vdt, m, row_offsets, col_idx, values, x, y, stream));
+    if (!aligned(col_idx, 4) || !aligned(values, value_bytes(vdt)) || !aligned(x, 4) || !aligned(y, 4))
+        return LB_ERR_INVALID_ARG;
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
-    const int T = merge_tile_items(t.threads, t.items_per_thread);
+    const int T = merge_tile_items(t.items_per_thread);
     const int G = num_tiles_of(m, nnz, T);
     // Workspace: tile_row[G+1], tile_nz[G+1], carry_row[G], carry_val[G].
     const size_t bytes = (2 * (static_cast<size_t>(G) + 1) + static_cast<size_t>(G)) * sizeof(int) +
@@ -300,10 +313,38 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
         a.carry_row = carry_row;
         a.carry_val = carry_val;
         a.err = err;
+        set_merge_alignment(a, value_bytes(vdt));
         e = launch_merge_spmv(vdt, kPlain, t.threads, t.items_per_thread, a, stream, g_ev_before, g_ev_after);
     }
     cudaError_t e2 = cudaFreeAsync(ws, stream);
     return from_cuda(e != cudaSuccess ? e : e2);
+}
+
+// The merge-path forward of a plan over its warp tiles (x_gathered may be null).
+static lb_status planned_forward(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
+                                 const float *x, float *y, float *x_gathered, cudaStream_t stream) {
+    if (!aligned(col_idx, 4) || !aligned(values, value_bytes(vdt)) || !aligned(x, 4) || !aligned(y, 4))
+        return LB_ERR_INVALID_ARG;
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    MergeArgs a{};
+    a.num_tiles = p->wG;
+    a.num_rows = p->m;
+    a.num_atoms = p->nnz;
+    a.tile_row = p->w_tile_row;
+    a.tile_nz = p->w_tile_nz;
+    a.row_end = p->ro + 1;
+    a.idx = col_idx;
+    a.val = values;
+    a.x = x;
+    a.y = y;
+    a.carry_row = p->w_carry_row;
+    a.carry_val = p->w_carry_val;
+    a.xg = x_gathered;
+    a.err = err;
+    set_merge_alignment(a, value_bytes(vdt));
+    return from_cuda(launch_merge_spmv(vdt, kPlain, p->tune.threads, p->tune.items_per_thread, a, stream, g_ev_before,
+                                       g_ev_after));
 }
 
 lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_schedule s, const lb_tuning *t,
@@ -325,7 +366,7 @@ lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_sched
     // The forward partition is built for every schedule (dvalues and the transpose use it).
     const int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
     const int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
-    p->tile_items = merge_tile_items(threads, ipt);
+    p->tile_items = cta_tile_items(threads, ipt);
     p->G = num_tiles_of(m, nnz, p->tile_items);
     cudaError_t e = cudaSuccess;
     if ((e = dmalloc(&p->ro, static_cast<size_t>(m) + 1)) != cudaSuccess ||
@@ -346,6 +387,16 @@ lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_sched
         e = cudaMemcpy(p->ro, zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_row, zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_nz, zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && m > 0) {
+        // Every plan holds the warp tiles: the merge-path forward runs over them, and so do the
+        // per-nonzero passes of the backward (the shape's items per lane, else 8).
+        p->w_tile_items = merge_tile_items(p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt);
+        p->wG = num_tiles_of(m, nnz, p->w_tile_items);
+        const size_t g = static_cast<size_t>(p->wG);
+        if ((e = dmalloc(&p->w_tile_row, g + 1)) == cudaSuccess && (e = dmalloc(&p->w_tile_nz, g + 1)) == cudaSuccess &&
+            (e = dmalloc(&p->w_carry_row, g)) == cudaSuccess && (e = dmalloc(&p->w_carry_val, g)) == cudaSuccess)
+            e = launch_partition(m, nnz, p->ro, p->w_tile_items, p->w_tile_row, p->w_tile_nz, stream);
     }
     if (e == cudaSuccess && p->sched == LB_SCHED_NONZERO_SPLIT && nnz > 0) {
         const int T = nzsplit_tile_nonzeros();
@@ -373,19 +424,48 @@ lb_status lb_plan_info(const lb_plan *p, lb_schedule *s, lb_tuning *t, int *num_
     return LB_OK;
 }
 
-lb_status lb_plan_partition(const lb_plan *p, int transposed, int *tile_row, int *tile_nz, int *num_tiles) {
-    if (!p || !num_tiles) return LB_ERR_INVALID_ARG;
-    if (transposed && !p->has_t) return LB_ERR_INVALID_ARG;
-    const int G = transposed ? p->Gt : p->G;
+// The plan's tile sets: LB_TILES_ROWS (block tiles of the passes over the forward partition),
+// LB_TILES_TRANSPOSED (warp tiles of the transposed product), LB_TILES_MERGE (warp tiles of
+// the merge-path forward).
+static bool plan_tiles(const lb_plan *p, int which, int *G, int *items, const int **tr, const int **tn) {
+    switch (which) {
+        case LB_TILES_ROWS:
+            *G = p->G, *items = p->tile_items, *tr = p->tile_row, *tn = p->tile_nz;
+            return true;
+        case LB_TILES_TRANSPOSED:
+            if (!p->has_t) return false;
+            *G = p->Gt, *items = p->t_tile_items, *tr = p->t_tile_row, *tn = p->t_tile_nz;
+            return true;
+        case LB_TILES_MERGE:
+            if (!p->w_tile_row) return false;
+            *G = p->wG, *items = p->w_tile_items, *tr = p->w_tile_row, *tn = p->w_tile_nz;
+            return true;
+        default:
+            return false;
+    }
+}
+
+lb_status lb_plan_tiles(const lb_plan *p, int which, int *num_tiles, int *tile_items) {
+    int G = 0, items = 0;
+    const int *tr = nullptr, *tn = nullptr;
+    if (!p || !plan_tiles(p, which, &G, &items, &tr, &tn)) return LB_ERR_INVALID_ARG;
+    if (num_tiles) *num_tiles = G;
+    if (tile_items) *tile_items = items;
+    return LB_OK;
+}
+
+lb_status lb_plan_partition(const lb_plan *p, int which, int *tile_row, int *tile_nz, int *num_tiles) {
+    int G = 0, items = 0;
+    const int *tr = nullptr, *tn = nullptr;
+    if (!p || !num_tiles || !plan_tiles(p, which, &G, &items, &tr, &tn)) return LB_ERR_INVALID_ARG;
     *num_tiles = G;
     if (!tile_row) return LB_OK;
     if (!tile_nz) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     cudaError_t e = cudaDeviceSynchronize();
     const size_t bytes = (static_cast<size_t>(G) + 1) * sizeof(int);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(tile_row, transposed ? p->t_tile_row : p->tile_row, bytes, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(tile_nz, transposed ? p->t_tile_nz : p->tile_nz, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tile_row, tr, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tile_nz, tn, bytes, cudaMemcpyDeviceToHost);
     return from_cuda(e);
 }
 
@@ -401,24 +481,7 @@ lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *valu
                                         y, p->nz_carry_row, p->nz_carry_val, stream));
     if (p->sched != LB_SCHED_MERGE_PATH)
         return from_cuda(launch_mapped(p->sched, p->tune, vdt, p->m, p->ro, col_idx, values, x, y, stream));
-    int *err = device_error_word();
-    if (!err) return LB_ERR_CUDA;
-    MergeArgs a{};
-    a.num_tiles = p->G;
-    a.num_rows = p->m;
-    a.num_atoms = p->nnz;
-    a.tile_row = p->tile_row;
-    a.tile_nz = p->tile_nz;
-    a.row_end = p->ro + 1;
-    a.idx = col_idx;
-    a.val = values;
-    a.x = x;
-    a.y = y;
-    a.carry_row = p->carry_row;
-    a.carry_val = p->carry_val;
-    a.err = err;
-    return from_cuda(launch_merge_spmv(vdt, kPlain, p->tune.threads, p->tune.items_per_thread, a, stream, g_ev_before,
-                                       g_ev_after));
+    return planned_forward(p, col_idx, values, vdt, x, y, nullptr, stream);
 }
 
 lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
@@ -429,25 +492,8 @@ lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void 
     if (!y || (p->nnz > 0 && (!col_idx || !values || !x || !x_gathered))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return from_cuda(cudaMemsetAsync(y, 0, static_cast<size_t>(p->m) * sizeof(float), stream));
-    int *err = device_error_word();
-    if (!err) return LB_ERR_CUDA;
-    MergeArgs a{};
-    a.num_tiles = p->G;
-    a.num_rows = p->m;
-    a.num_atoms = p->nnz;
-    a.tile_row = p->tile_row;
-    a.tile_nz = p->tile_nz;
-    a.row_end = p->ro + 1;
-    a.idx = col_idx;
-    a.val = values;
-    a.x = x;
-    a.y = y;
-    a.carry_row = p->carry_row;
-    a.carry_val = p->carry_val;
-    a.xg = x_gathered;
-    a.err = err;
-    return from_cuda(launch_merge_spmv(vdt, kPlain, p->tune.threads, p->tune.items_per_thread, a, stream, g_ev_before,
-                                       g_ev_after));
+    if (!aligned(x_gathered, 4)) return LB_ERR_INVALID_ARG;
+    return planned_forward(p, col_idx, values, vdt, x, y, x_gathered, stream);
 }
 
 lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t stream) {
@@ -471,7 +517,8 @@ lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t s
         if (e != cudaSuccess) return from_cuda(e);
         if (h_status != 0) return LB_ERR_BAD_MATRIX;
     }
-    p->Gt = num_tiles_of(n, nnz, p->tile_items);
+    p->t_tile_items = merge_tile_items(kDefaultIpt);
+    p->Gt = num_tiles_of(n, nnz, p->t_tile_items);
     if ((e = dmalloc(&p->co, static_cast<size_t>(n) + 1)) != cudaSuccess ||
         (e = dmalloc(&p->ri, static_cast<size_t>(nnz))) != cudaSuccess ||
         (e = dmalloc(&p->perm, static_cast<size_t>(nnz))) != cudaSuccess ||
@@ -496,7 +543,7 @@ lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t s
     }
     if (e == cudaSuccess) {
         if (n > 0) {
-            e = launch_partition(n, nnz, p->co, p->tile_items, p->t_tile_row, p->t_tile_nz, stream);
+            e = launch_partition(n, nnz, p->co, p->t_tile_items, p->t_tile_row, p->t_tile_nz, stream);
         } else {
             e = cudaMemsetAsync(p->t_tile_row, 0, sizeof(int), stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(p->t_tile_nz, 0, sizeof(int), stream);
@@ -530,8 +577,8 @@ static lb_status transposed_product(const lb_plan *p, const void *values, lb_dty
                                     const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream) {
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
-    cudaError_t e = launch_csr_backward(vdt, p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, g, values,
-                                        p->bucket_pos, p->pv, x_gathered, dvalues, stream);
+    cudaError_t e = launch_csr_backward(vdt, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row, p->w_tile_nz,
+                                        p->ro + 1, g, values, p->bucket_pos, p->pv, x_gathered, dvalues, stream);
     if (e != cudaSuccess) return from_cuda(e);
     MergeArgs a{};
     a.num_tiles = p->Gt;
@@ -546,17 +593,11 @@ static lb_status transposed_product(const lb_plan *p, const void *values, lb_dty
     a.carry_row = p->t_carry_row;
     a.carry_val = p->t_carry_val;
     a.err = err;
-    int threads = p->sched == LB_SCHED_MERGE_PATH ? p->tune.threads : kDefaultThreads;
-    int ipt = p->sched == LB_SCHED_MERGE_PATH ? p->tune.items_per_thread : kDefaultIpt;
-    // The gather-sum stages no values, and on GB300 it runs fastest as 256 x 8 (318 us on the
-    // 4M-row power-law matrix, against 377 us at 256 x 16).  Any shape with the plan's tile
-    // size can run the transposed partition, so a plan tuned to 128 x 16 for its forward
-    // (narrow values) keeps 256 x 8 here.
-    if (merge_tile_items(kDefaultThreads, kDefaultIpt) == p->tile_items) {
-        threads = kDefaultThreads;
-        ipt = kDefaultIpt;
-    }
-    return from_cuda(launch_merge_spmv(LB_F32, kGatherSum, threads, ipt, a, stream, g_ev_before, g_ev_after));
+    set_merge_alignment(a, 0);
+    // The gather-sum streams only its positions, whatever the plan's forward shape: it always
+    // runs the default (256, 8) shape over the transposed warp tiles.
+    return from_cuda(
+        launch_merge_spmv(LB_F32, kGatherSum, kDefaultThreads, kDefaultIpt, a, stream, g_ev_before, g_ev_after));
 }
 
 lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
@@ -588,8 +629,9 @@ lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const v
     if (p->n == 0) return LB_OK;
     cudaError_t e = cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream);
     if (e != cudaSuccess || p->nnz == 0) return from_cuda(e);
-    return from_cuda(launch_csr_backward_scatter(vdt, p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, g,
-                                                 values, col_idx, dx, x_gathered, dvalues, stream));
+    return from_cuda(launch_csr_backward_scatter(vdt, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row,
+                                                 p->w_tile_nz, p->ro + 1, g, values, col_idx, dx, x_gathered, dvalues,
+                                                 stream));
 }
 
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
@@ -598,8 +640,8 @@ lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, 
     if (p->nnz == 0) return LB_OK;
     if (!col_idx || !g || !x || !dvalues) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(launch_dvalues(p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, nullptr,
-                                    dvalues, stream));
+    return from_cuda(
+        launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, dvalues, stream));
 }
 
 lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
@@ -608,8 +650,8 @@ lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float
     if (p->nnz == 0) return LB_OK;
     if (!g || !x_gathered || !dvalues) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(launch_dvalues(p->G, p->m, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, nullptr, g, nullptr,
-                                    x_gathered, dvalues, stream));
+    return from_cuda(launch_csr_backward(LB_F32, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row, p->w_tile_nz,
+                                         p->ro + 1, g, nullptr, nullptr, nullptr, x_gathered, dvalues, stream));
 }
 
 lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, int kc, const float *B,
@@ -682,7 +724,7 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     p->total_cols = cols;
     p->total_nnz = nnz;
     p->tune = r;
-    p->tile_items = merge_tile_items(r.threads, r.items_per_thread);
+    p->tile_items = merge_tile_items(r.items_per_thread);
     p->G = num_tiles_of(rows, nnz, p->tile_items);
     const int kc = p->kc;
     int *d_ro_pos = nullptr, *d_row_base = nullptr;
@@ -765,6 +807,9 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, c
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->total_nnz == 0)
         return from_cuda(cudaMemsetAsync(y_concat, 0, static_cast<size_t>(p->total_rows) * sizeof(float), stream));
+    if (!aligned(col_idx_concat, 4) || !aligned(values_concat, value_bytes(vdt)) || !aligned(x_concat, 4) ||
+        !aligned(y_concat, 4))
+        return LB_ERR_INVALID_ARG;
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
     MergeArgs a{};
@@ -784,6 +829,7 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, c
     a.mat_col_base = p->mat_col_base;
     a.tile_mat = p->tile_mat;
     a.err = err;
+    set_merge_alignment(a, value_bytes(vdt));
     return from_cuda(launch_merge_spmv(vdt, kBatched, p->tune.threads, p->tune.items_per_thread, a, stream,
                                        g_ev_before, g_ev_after));
 }
@@ -830,6 +876,19 @@ lb_status lb_device_error(int *status, int clear) {
 }  // extern "C"
 
 namespace lb {
+
+void set_merge_alignment(MergeArgs &a, size_t value_bytes) {
+    // The kernel's lanes start 32-byte aligned in the index array; the values (and the saved
+    // gathers) take the same vector loads and stores when their own phase matches.
+    const uintptr_t ip = reinterpret_cast<uintptr_t>(a.idx);
+    const uintptr_t iph = (ip >> 2) & 7u;
+    const uintptr_t vp = reinterpret_cast<uintptr_t>(a.val);
+    const uintptr_t xp = reinterpret_cast<uintptr_t>(a.xg);
+    a.vec_vals = 0;
+    if (a.val && value_bytes == 4) a.vec_vals = (vp & 3u) == 0 && ((vp >> 2) & 7u) == iph;
+    if (a.val && value_bytes == 2) a.vec_vals = (vp & 1u) == 0 && ((vp >> 1) & 7u) == iph;
+    a.vec_xg = a.xg != nullptr && (xp & 3u) == 0 && ((xp >> 2) & 7u) == iph;
+}
 
 cudaError_t launch_merge_spmv(lb_dtype vdt, int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t stream,
                               cudaEvent_t ev_before, cudaEvent_t ev_after) {

@@ -4,7 +4,7 @@
 // reductions into dx).
 #include <cstdint>
 
-#include "lb_internal.cuh"
+#include "lb_warp.cuh"
 
 namespace lb {
 
@@ -88,271 +88,288 @@ static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, 
     return cudaGetLastError();
 }
 
-// One streaming pass over the nonzeros in CSR order, tile by tile over the forward partition:
+// One streaming pass over the nonzeros in CSR order, warp tile by warp tile over the forward
+// merge-path partition (every warp independent, no block-wide barrier):
 //   pv[pos(k)] = values[k] * g[row(k)]   (pos = bucket_pos, or the identity), when pv is given;
-//   dv[k]      = g[row(k)] * xg[k]        (the values gradient from saved gathers), when dv is.
-// The rows come without any search: every row end inside the tile adds 1 to a per-slot count
-// in shared memory, and a slot's row is the inclusive prefix sum of the counts (each thread
-// sums its IPT slots, the block scans the thread totals).  Slot 0 of a tile sits 16 bytes
-// aligned in the nonzero arrays (the tile's first nonzero at slot `lead`), so each thread
-// moves its IPT consecutive entries with vector loads and stores where the arrays allow.  The
-// scaled values go to shared memory and out in a second, lane-consecutive pass, so that the
-// scattered bucket positions of neighbouring nonzeros coalesce as well as they can.
-template <typename V, int IPT>
-__device__ __forceinline__ void load_values(const V *src, bool vec, bool full, int j0, int nk, float (&o)[IPT]) {
-    if (full && vec) {
-        if constexpr (sizeof(V) == 4) {
-#pragma unroll
-            for (int q = 0; q < IPT; q += 4) {
-                const float4 t = __ldcs(reinterpret_cast<const float4 *>(src + q));
-                o[q] = t.x;
-                o[q + 1] = t.y;
-                o[q + 2] = t.z;
-                o[q + 3] = t.w;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < IPT; q += 4) {
-                const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(src + q));
-                const uint32_t w[2] = {t.x, t.y};
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    V lo, hi;
-                    const unsigned short bl = static_cast<unsigned short>(w[e] & 0xffffu);
-                    const unsigned short bh = static_cast<unsigned short>(w[e] >> 16);
-                    memcpy(&lo, &bl, 2);
-                    memcpy(&hi, &bh, 2);
-                    o[q + 2 * e] = to_f32(lo);
-                    o[q + 2 * e + 1] = to_f32(hi);
-                }
-            }
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < IPT; ++q) o[q] = (j0 + q >= 0 && j0 + q < nk) ? to_f32(src[q]) : 0.f;
-    }
-}
+//   dv[k]      = g[row(k)] * xg[k]        (the values gradient from saved gathers), when dv is;
+//   dx[ci[k]] += values[k] * g[row(k)]    (float reductions, SCATTER only).
+// Lane l owns the tile's slots [8 l, 8 l + 8); slot 0 sits 32 bytes aligned in the nonzero
+// arrays (the tile's first nonzero at slot lead = k0 mod 8), so every lane moves its eight
+// values, saved gathers and dvalues with one 256-bit (values: 128-bit when 16-bit) access.
+// The rows come without a search: each row end inside the tile adds 1 to a per-slot count
+// in the warp's shared memory, and a slot's row is r0 plus the inclusive prefix sum of the
+// counts (in the lane, then across lanes by shuffles).  The scaled values leave through the
+// warp's shared memory in a lane-consecutive pass, so that the bucket positions of
+// neighbouring nonzeros (consecutive inside a bucket) coalesce.
+struct CsrBackwardArgs {
+    int G, m, nnz;
+    const int *tile_row, *tile_nz, *row_end;
+    const float *g;
+    const void *values;
+    const int *bucket_pos;  // null: pv in CSR order
+    float *pv;              // null: no scaled values
+    const float *xg;        // saved gathers (with dv)
+    float *dv;              // null: no values gradient
+    const int *ci;          // SCATTER: column indices
+    float *dx;              // SCATTER: dx accumulated by float reductions
+    int vec_v, vec_xg, vec_dv, vec_ci;  // the arrays' bases are 32-byte (16-bit values: 16-byte) aligned
+};
 
+// Per warp: per-slot row-end counts, then the padded buffer of scaled values.
 template <int IPT>
-__device__ __forceinline__ void load_ints(const int *src, bool vec, bool full, int j0, int nk, int (&o)[IPT]) {
-    if (full && vec) {
-#pragma unroll
-        for (int q = 0; q < IPT; q += 4) {
-            const int4 t = __ldcs(reinterpret_cast<const int4 *>(src + q));
-            o[q] = t.x;
-            o[q + 1] = t.y;
-            o[q + 2] = t.z;
-            o[q + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < IPT; ++q) o[q] = (j0 + q >= 0 && j0 + q < nk) ? __ldcs(src + q) : 0;
-    }
+__host__ __device__ constexpr int csr_warp_bytes() {
+    return WarpTile<IPT>::SLOTS * 4 + WarpTile<IPT>::VALS * 4;
 }
 
-// SCATTER: instead of the bucketed scaled values, add each v[k] * g[row(k)] into dx[col(k)]
-// with a float reduction in L2 (dx must start at zero).  No CSC view is needed; the sums of a
-// column then arrive in no fixed order, so dx is not bit-reproducible (it stays within the
-// FP32 tolerance of the transposed product).
-template <typename V, int THREADS, int IPT, bool SCATTER>
-__global__ void __launch_bounds__(THREADS) csr_backward_kernel(int G, int m, const int *__restrict__ tile_row,
-                                                               const int *__restrict__ tile_nz,
-                                                               const int *__restrict__ row_end,
-                                                               const float *__restrict__ g,
-                                                               const V *__restrict__ values,
-                                                               const int *__restrict__ bucket_pos,
-                                                               float *__restrict__ pv, const float *__restrict__ xg,
-                                                               float *__restrict__ dv, const int *__restrict__ ci,
-                                                               float *__restrict__ dx_acc) {
-    constexpr int T = THREADS * IPT;
-    constexpr int WARPS = THREADS / 32;
-    static_assert(IPT % 4 == 0, "slots move four at a time");
-    __shared__ __align__(16) int cnt[T];
-    __shared__ __align__(16) float s_pv[T];
-    __shared__ int wsum[WARPS];
-    for (int i = threadIdx.x; i < T; i += THREADS) cnt[i] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool want_pv = !SCATTER && pv != nullptr, want_dv = dv != nullptr;
-    const bool vec_ci = (reinterpret_cast<uintptr_t>(ci) & 15u) == 0;
-    // Slot 0 of every tile is 16-byte aligned in an array whose base is (4-byte elements) or
-    // 8-byte aligned (2-byte values, moved four at a time).
-    const bool vec_xg = (reinterpret_cast<uintptr_t>(xg) & 15u) == 0;
-    const bool vec_dv = (reinterpret_cast<uintptr_t>(dv) & 15u) == 0;
-    const bool vec_v = (reinterpret_cast<uintptr_t>(values) & (sizeof(V) == 4 ? 15u : 7u)) == 0;
-    for (int tile = blockIdx.x; tile < G; tile += gridDim.x) {
-        const int r0 = __ldg(tile_row + tile), r1 = __ldg(tile_row + tile + 1);
-        const int k0 = __ldg(tile_nz + tile), k1 = __ldg(tile_nz + tile + 1);
+template <typename V, int IPT, bool SCATTER>
+__global__ void __launch_bounds__(256) csr_backward_kernel(const CsrBackwardArgs a) {
+    constexpr int SLOTS = WarpTile<IPT>::SLOTS;
+    constexpr int WB = csr_warp_bytes<IPT>();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int *cnt = reinterpret_cast<int *>(smem + wib * WB);
+    float *buf = reinterpret_cast<float *>(smem + wib * WB + SLOTS * 4);
+    const int nw = static_cast<int>(gridDim.x) * (blockDim.x >> 5);
+    int t = static_cast<int>(blockIdx.x) * (blockDim.x >> 5) + wib;
+    if (t >= a.G) return;
+#pragma unroll
+    for (int q = 0; q < IPT; q += 4) *reinterpret_cast<int4 *>(cnt + IPT * lane + q) = make_int4(0, 0, 0, 0);
+    __syncwarp();
+    const uint64_t pol = policy_evict_first();
+    const bool want_pv = !SCATTER && a.pv != nullptr, want_dv = a.dv != nullptr;
+    int bw = lane < 2 ? __ldg(a.tile_row + t + lane) : (lane < 4 ? __ldg(a.tile_nz + t + lane - 2) : 0);
+    for (; t < a.G; t += nw) {
+        const int r0 = __shfl_sync(0xffffffffu, bw, 0), r1 = __shfl_sync(0xffffffffu, bw, 1);
+        const int k0 = __shfl_sync(0xffffffffu, bw, 2), k1 = __shfl_sync(0xffffffffu, bw, 3);
+        if (t + nw < a.G)
+            bw = lane < 2 ? __ldg(a.tile_row + t + nw + lane) : (lane < 4 ? __ldg(a.tile_nz + t + nw + lane - 2) : 0);
         const int nr = r1 - r0, nk = k1 - k0;
-        const int lead = k0 & 3;  // nonzero k0 - lead is a multiple of 4
-        if (nr < 0 || nk < 0 || nk + lead > T) continue;  // malformed offsets (block-uniform)
-        const int s0 = threadIdx.x * IPT;
-        const int j0 = s0 - lead;  // tile item of this thread's first slot
-        const bool mine = j0 + IPT > 0 && j0 < nk;
-        const bool full = j0 >= 0 && j0 + IPT <= nk;
-        // Every load that does not depend on the rows goes out first, so its latency overlaps
-        // the row-end staging and the scan: this thread's values and saved gathers (blocked)
-        // and the bucket positions of the lane-consecutive scatter.
+        if (r0 < 0 || nr < 0 || r1 > a.m || k0 < 0 || nk < 0 || k1 > a.nnz || nr + nk > WarpTile<IPT>::ITEMS)
+            continue;  // malformed offsets (warp-uniform): nothing is read or written
+        const int lead = k0 & 7;
+        const int kb = k0 - lead;
+        const int e0 = kb + IPT * lane;
+        const uint32_t vm = slot_mask<IPT>(e0, k0, k1);
+        const bool inb = e0 >= 0 && e0 + IPT <= a.nnz;  // the lane's eight elements exist
+        // Every load that does not depend on the rows goes out first.
         float vv[IPT], xv[IPT];
-        int bp[IPT], cc[IPT];
-        if ((want_pv || SCATTER) && mine) load_values<V, IPT>(values + k0 + j0, vec_v, full, j0, nk, vv);
-        if (want_dv && mine) load_values<float, IPT>(xg + k0 + j0, vec_xg, full, j0, nk, xv);
-        if (SCATTER && mine) load_ints<IPT>(ci + k0 + j0, vec_ci, full, j0, nk, cc);
-        if (want_pv) {
+        int cc[IPT], bp[IPT];
 #pragma unroll
-            for (int u = 0; u < IPT; ++u) {
-                const int j = threadIdx.x + u * THREADS;
-                bp[u] = j < nk ? (bucket_pos != nullptr ? __ldcs(bucket_pos + k0 + j) : k0 + j) : 0;
-            }
-        }
-        for (int r = threadIdx.x; r < nr; r += THREADS) {
-            const int e = __ldg(row_end + r0 + r) - k0;  // first nonzero of the next row, tile-local
-            if (e >= 0 && e < nk) atomicAdd(&cnt[e + lead], 1);
-        }
-        __syncthreads();
-        int c[IPT];
+        for (int q = 0; q < IPT; ++q) vv[q] = xv[q] = 0.f, cc[q] = bp[q] = 0;
+        if ((want_pv || SCATTER) && vm) {
+            if (sizeof(V) == 4) {
+                const float *v = static_cast<const float *>(a.values);
+                if (a.vec_v && inb) {
 #pragma unroll
-        for (int q = 0; q < IPT; q += 4) {
-            const int4 t = *reinterpret_cast<const int4 *>(cnt + s0 + q);
-            c[q] = t.x;
-            c[q + 1] = t.y;
-            c[q + 2] = t.z;
-            c[q + 3] = t.w;
-            *reinterpret_cast<int4 *>(cnt + s0 + q) = make_int4(0, 0, 0, 0);  // ready for the next tile
-        }
+                    for (int h = 0; h < IPT; h += 8) {
+                        uint32_t r[8];
+                        ld_stream8(v + e0 + h, pol, r);
 #pragma unroll
-        for (int q = 1; q < IPT; ++q) c[q] += c[q - 1];
-        const int tot = c[IPT - 1];
-        int incl = tot;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        int base = incl - tot;
-        for (int w = 0; w < warp; ++w) base += wsum[w];
-        if (mine) {
-            float gq[IPT];
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                const int row = r0 + base + c[q];
-                gq[q] = (j0 + q >= 0 && j0 + q < nk && row < m) ? __ldg(g + row) : 0.f;
-            }
-            if (SCATTER) {
-#pragma unroll
-                for (int q = 0; q < IPT; ++q)
-                    if (j0 + q >= 0 && j0 + q < nk) atomicAdd(dx_acc + cc[q], vv[q] * gq[q]);
-            }
-            if (want_pv) {
-#pragma unroll
-                for (int q = 0; q < IPT; q += 4)
-                    *reinterpret_cast<float4 *>(s_pv + s0 + q) =
-                        make_float4(vv[q] * gq[q], vv[q + 1] * gq[q + 1], vv[q + 2] * gq[q + 2], vv[q + 3] * gq[q + 3]);
-            }
-            if (want_dv) {
-                float *dst = dv + k0 + j0;
-                if (full && vec_dv) {
-#pragma unroll
-                    for (int q = 0; q < IPT; q += 4)
-                        __stcs(reinterpret_cast<float4 *>(dst + q),
-                               make_float4(gq[q] * xv[q], gq[q + 1] * xv[q + 1], gq[q + 2] * xv[q + 2],
-                                           gq[q + 3] * xv[q + 3]));
+                        for (int q = 0; q < 8; ++q) vv[h + q] = __uint_as_float(r[q]);
+                    }
                 } else {
 #pragma unroll
                     for (int q = 0; q < IPT; ++q)
-                        if (j0 + q >= 0 && j0 + q < nk) __stcs(dst + q, gq[q] * xv[q]);
+                        if ((vm >> q) & 1u) vv[q] = __ldg(v + e0 + q);
+                }
+            } else {
+                const unsigned short *v = static_cast<const unsigned short *>(a.values);
+                if (a.vec_v && inb) {
+#pragma unroll
+                    for (int h = 0; h < IPT; h += 8) {
+                        uint32_t r[4];
+                        ld_stream4(v + e0 + h, pol, r);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            vv[h + 2 * q] = half_bits_to_f32<V>(r[q] & 0xffffu);
+                            vv[h + 2 * q + 1] = half_bits_to_f32<V>(r[q] >> 16);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if ((vm >> q) & 1u) vv[q] = half_bits_to_f32<V>(__ldg(v + e0 + q));
                 }
             }
         }
-        if (want_pv) {
-            __syncthreads();
+        if (want_dv && vm) {
+            if (a.vec_xg && inb) {
 #pragma unroll
-            for (int u = 0; u < IPT; ++u) {
-                const int j = threadIdx.x + u * THREADS;
-                if (j < nk) pv[bp[u]] = s_pv[j + lead];
+                for (int h = 0; h < IPT; h += 8) {
+                    uint32_t r[8];
+                    ld_stream8(a.xg + e0 + h, pol, r);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) xv[h + q] = __uint_as_float(r[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if ((vm >> q) & 1u) xv[q] = __ldg(a.xg + e0 + q);
             }
         }
-        __syncthreads();  // the counts, wsum and s_pv are reused by the next tile
+        if (SCATTER && vm) {
+            if (a.vec_ci && inb) {
+#pragma unroll
+                for (int h = 0; h < IPT; h += 8) {
+                    uint32_t r[8];
+                    ld_stream8(a.ci + e0 + h, pol, r);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cc[h + q] = static_cast<int>(r[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if ((vm >> q) & 1u) cc[q] = __ldg(a.ci + e0 + q);
+            }
+        }
+        if (want_pv) {  // lane-consecutive: slot j = 32 q + lane
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int j = 32 * q + lane;
+                if (j >= lead && j < lead + nk)
+                    bp[q] = a.bucket_pos != nullptr ? __ldcs(a.bucket_pos + kb + j) : kb + j;
+            }
+        }
+        // Rows: each row end inside the tile counts at the slot of the next row's first nonzero.
+        for (int j = 0; j < nr; j += 32) {
+            if (j + lane < nr) {
+                const int e = __ldg(a.row_end + r0 + j + lane);
+                if (e >= k0 && e < k1) atomicAdd(cnt + (e - kb), 1);
+            }
+        }
+        __syncwarp();
+        int c[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; q += 4) {
+            const int4 cq = *reinterpret_cast<const int4 *>(cnt + IPT * lane + q);
+            *reinterpret_cast<int4 *>(cnt + IPT * lane + q) = make_int4(0, 0, 0, 0);
+            c[q] = cq.x, c[q + 1] = cq.y, c[q + 2] = cq.z, c[q + 3] = cq.w;
+        }
+#pragma unroll
+        for (int q = 1; q < IPT; ++q) c[q] += c[q - 1];
+        int incl = c[IPT - 1];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
+        }
+        const int base = r0 + incl - c[IPT - 1];
+        float gq[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const int row = base + c[q];
+            gq[q] = (((vm >> q) & 1u) && row < a.m) ? __ldg(a.g + row) : 0.f;
+        }
+        if (want_dv && vm) {
+            float d[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) d[q] = gq[q] * xv[q];
+            if (vm == (1u << IPT) - 1u && a.vec_dv) {
+#pragma unroll
+                for (int h = 0; h < IPT; h += 8) st_stream8(a.dv + e0 + h, pol, d + h);
+            } else {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q)
+                    if ((vm >> q) & 1u) __stcs(a.dv + e0 + q, d[q]);
+            }
+        }
+        if (SCATTER) {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q)
+                if ((vm >> q) & 1u) atomicAdd(a.dx + cc[q], vv[q] * gq[q]);
+        }
+        if (want_pv) {
+#pragma unroll
+            for (int q = 0; q < IPT; q += 4)
+                *reinterpret_cast<float4 *>(buf + ppad(IPT * lane + q)) =
+                    make_float4(vv[q] * gq[q], vv[q + 1] * gq[q + 1], vv[q + 2] * gq[q + 2], vv[q + 3] * gq[q + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int j = 32 * q + lane;
+                if (j >= lead && j < lead + nk) a.pv[bp[q]] = buf[ppad(j)];
+            }
+        }
+        __syncwarp();  // the counts and the buffer are reused by the next tile
     }
 }
 
+template <typename V, int IPT, bool SCATTER>
+static cudaError_t launch_csr_backward_ipt(CsrBackwardArgs a, cudaStream_t stream) {
+    // One wave of resident warps (each loops over its tiles).
+    auto kern = csr_backward_kernel<V, IPT, SCATTER>;
+    constexpr int threads = 256;
+    const size_t smem = static_cast<size_t>(threads / 32) * csr_warp_bytes<IPT>();
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
+    const long long need = (static_cast<long long>(a.G) + threads / 32 - 1) / (threads / 32);
+    if (grid > need) grid = need;
+    const size_t vb = (sizeof(V) == 4) ? 31u : 15u;
+    a.vec_v = (reinterpret_cast<uintptr_t>(a.values) & vb) == 0;
+    a.vec_xg = (reinterpret_cast<uintptr_t>(a.xg) & 31u) == 0;
+    a.vec_dv = (reinterpret_cast<uintptr_t>(a.dv) & 31u) == 0;
+    a.vec_ci = (reinterpret_cast<uintptr_t>(a.ci) & 31u) == 0;
+    kern<<<static_cast<int>(grid), threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// The warp tiles' size picks the slots per lane: tiles of merge_tile_items(8) or (16) items.
 template <typename V, bool SCATTER>
-static cudaError_t launch_csr_backward_t(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
-                                         const int *row_end, const float *g, const V *values, const int *bucket_pos,
-                                         float *pv, const float *xg, float *dv, const int *ci, float *dx_acc,
-                                         cudaStream_t stream) {
-    // One wave of resident CTAs (the kernel loops over tiles).  A tile's slots: its items plus
-    // a lead of up to 3 must fit.
-    auto launch = [&](auto kern, int threads) -> cudaError_t {
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
-        if (e != cudaSuccess) return e;
-        long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
-        if (grid > num_tiles) grid = num_tiles;
-        kern<<<static_cast<int>(grid), threads, 0, stream>>>(num_tiles, m, tile_row, tile_nz, row_end, g, values,
-                                                             bucket_pos, pv, xg, dv, ci, dx_acc);
-        return cudaGetLastError();
-    };
-    if (tile_items + 3 <= 2048) return launch(csr_backward_kernel<V, 256, 8, SCATTER>, 256);
-    if (tile_items + 3 <= 4096) return launch(csr_backward_kernel<V, 512, 8, SCATTER>, 512);
+static cudaError_t launch_csr_backward_t(CsrBackwardArgs a, int tile_items, cudaStream_t stream) {
+    if (tile_items <= merge_tile_items(8)) return launch_csr_backward_ipt<V, 8, SCATTER>(a, stream);
+    if (tile_items <= merge_tile_items(16)) return launch_csr_backward_ipt<V, 16, SCATTER>(a, stream);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz, const int *tile_row,
                                 const int *tile_nz, const int *row_end, const float *g, const void *values,
                                 const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream) {
     if (num_tiles <= 0) return cudaSuccess;
     if ((pv != nullptr && values == nullptr) || (dv != nullptr && xg == nullptr)) return cudaErrorInvalidValue;
+    CsrBackwardArgs a{};
+    a.G = num_tiles, a.m = m, a.nnz = nnz;
+    a.tile_row = tile_row, a.tile_nz = tile_nz, a.row_end = row_end, a.g = g, a.values = values;
+    a.bucket_pos = bucket_pos, a.pv = pv, a.xg = xg, a.dv = dv;
     switch (vdt) {
         case LB_F32:
-            return launch_csr_backward_t<float, false>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                       static_cast<const float *>(values), bucket_pos, pv, xg, dv,
-                                                       nullptr, nullptr, stream);
+            return launch_csr_backward_t<float, false>(a, tile_items, stream);
         case LB_BF16:
-            return launch_csr_backward_t<__nv_bfloat16, false>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                               static_cast<const __nv_bfloat16 *>(values), bucket_pos,
-                                                               pv, xg, dv, nullptr, nullptr, stream);
+            return launch_csr_backward_t<__nv_bfloat16, false>(a, tile_items, stream);
         case LB_F16:
-            return launch_csr_backward_t<__half, false>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                        static_cast<const __half *>(values), bucket_pos, pv, xg, dv,
-                                                        nullptr, nullptr, stream);
+            return launch_csr_backward_t<__half, false>(a, tile_items, stream);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz,
+                                        const int *tile_row,
                                         const int *tile_nz, const int *row_end, const float *g, const void *values,
                                         const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream) {
     if (num_tiles <= 0) return cudaSuccess;
     if (values == nullptr || ci == nullptr || dx == nullptr || (dv != nullptr && xg == nullptr))
         return cudaErrorInvalidValue;
+    CsrBackwardArgs a{};
+    a.G = num_tiles, a.m = m, a.nnz = nnz;
+    a.tile_row = tile_row, a.tile_nz = tile_nz, a.row_end = row_end, a.g = g, a.values = values;
+    a.xg = xg, a.dv = dv, a.ci = ci, a.dx = dx;
     switch (vdt) {
         case LB_F32:
-            return launch_csr_backward_t<float, true>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                      static_cast<const float *>(values), nullptr, nullptr, xg, dv, ci,
-                                                      dx, stream);
+            return launch_csr_backward_t<float, true>(a, tile_items, stream);
         case LB_BF16:
-            return launch_csr_backward_t<__nv_bfloat16, true>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                              static_cast<const __nv_bfloat16 *>(values), nullptr,
-                                                              nullptr, xg, dv, ci, dx, stream);
+            return launch_csr_backward_t<__nv_bfloat16, true>(a, tile_items, stream);
         case LB_F16:
-            return launch_csr_backward_t<__half, true>(num_tiles, m, tile_items, tile_row, tile_nz, row_end, g,
-                                                       static_cast<const __half *>(values), nullptr, nullptr, xg, dv,
-                                                       ci, dx, stream);
+            return launch_csr_backward_t<__half, true>(a, tile_items, stream);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_dvalues(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, const float *xg,
-                           float *dv, cudaStream_t stream) {
-    if (xg == nullptr)
-        return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, dv, nullptr,
-                                       stream);
-    return launch_csr_backward(LB_F32, num_tiles, m, tile_items, tile_row, tile_nz, row_end, g, nullptr, nullptr,
-                               nullptr, xg, dv, stream);
+cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
+                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
+                           cudaStream_t stream) {
+    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, dv, nullptr, stream);
 }
 
 cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,

@@ -147,7 +147,16 @@ struct MergeArgs {
     const int *tile_mat;      // batched: [G+1] matrix holding each tile's first nonzero
     float *xg;                // plain only, may be null: xg[k] = x[idx[k]] is saved for every atom
     int *err;                 // device error word
+    int vec_vals;             // val has the same 32-byte phase as idx (FP32) or 16-byte phase (16-bit)
+    int vec_xg;               // xg has the same 32-byte phase as idx
 };
+
+// Work items per merge-path tile of the warp-tiled kernel: 32 lanes x `ipt` slots, less 8
+// kept for the lead of a tile's first nonzero past a 32-byte boundary.
+__host__ __device__ constexpr int merge_tile_items(int ipt) { return 32 * ipt - 8; }
+
+// The alignment flags of MergeArgs, from the arrays' addresses.
+void set_merge_alignment(MergeArgs &a, size_t value_bytes);
 
 // kPlain: y[r] = sum of val[k] * x[idx[k]] over row r.  kBatched: the same over a batch, with
 // per-matrix column bases.  kGatherSum: y[r] = sum of x[idx[k]] (no values; the transposed
@@ -166,6 +175,12 @@ cudaError_t launch_merge_bf16(int mode, int threads, int ipt, const MergeArgs &a
 cudaError_t launch_merge_f16(int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t s,
                              cudaEvent_t eb, cudaEvent_t ea);
 
+// The host-side set-up of the plain merge-path product of one value type and shape (done by
+// the first launch otherwise).
+cudaError_t prepare_merge_f32(int threads, int ipt);
+cudaError_t prepare_merge_bf16(int threads, int ipt);
+cudaError_t prepare_merge_f16(int threads, int ipt);
+
 // Fixup: y[r] += sum of the carries of row r, for every carry row r < num_rows.
 cudaError_t launch_fixup(int num_tiles, int num_rows, const int *carry_row, const float *carry_val,
                          float *y, cudaStream_t stream);
@@ -178,11 +193,10 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
 cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, const int *ro,
                           const int *ci, const void *v, const float *x, float *y, cudaStream_t stream);
 
-// dvalues over the forward partition: dv[k] = g[row(k)] * x[ci[k]], or, with xg non-null,
-// dv[k] = g[row(k)] * xg[k] from x gathers saved by the forward product (ci and x unused).
-cudaError_t launch_dvalues(int num_tiles, int m, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, const float *xg,
-                           float *dv, cudaStream_t stream);
+// dvalues over the forward block tiles, gathering x: dv[k] = g[row(k)] * x[ci[k]].
+cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
+                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
+                           cudaStream_t stream);
 
 // Stable CSR -> CSC transpose (deterministic LSD radix sort by column).
 struct TransposeOut {
@@ -201,19 +215,21 @@ int value_bucket_shift(long long nnz);
 // bucket order of the entry CSC entry p needs), from perm.
 cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket_pos, int *bucket_perm,
                                 cudaStream_t stream);
-// One streaming pass over the nonzeros in CSR order (forward partition): the scaled values
-// pv[pos(k)] = values[k] * g[row(k)] with pos = bucket_pos (identity when null), and, when xg
-// and dv are given, dv[k] = g[row(k)] * xg[k].
-cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+// One streaming pass over the nonzeros in CSR order, over the forward's warp tiles (merge-path
+// tiles of merge_tile_items(8) or (16) items): the scaled values pv[pos(k)] = values[k] *
+// g[row(k)] with pos = bucket_pos (identity when null), when pv is given, and
+// dv[k] = g[row(k)] * xg[k] when xg and dv are given.
+cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz, const int *tile_row,
                                 const int *tile_nz, const int *row_end, const float *g, const void *values,
                                 const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream);
 
-// rowid[k] = the row of nonzero k, over the forward partition.
+// rowid[k] = the row of nonzero k, over the forward block tiles.
 cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
                                 const int *row_end, int *rowid, cudaStream_t stream);
 // The same pass adding v[k] * g[row(k)] into dx[col_idx[k]] with float reductions (dx zeroed
 // by the caller; not bit-reproducible), and dv[k] = g[row(k)] * xg[k] when dv is given.
-cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int m, int tile_items, const int *tile_row,
+cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz,
+                                        const int *tile_row,
                                         const int *tile_nz, const int *row_end, const float *g, const void *values,
                                         const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream);
 

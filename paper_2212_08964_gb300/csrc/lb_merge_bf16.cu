@@ -9,4 +9,6 @@ cudaError_t launch_merge_bf16(int mode, int threads, int ipt, const MergeArgs &a
     return dispatch_merge<__nv_bfloat16>(mode, threads, ipt, a, s, eb, ea);
 }
 
+cudaError_t prepare_merge_bf16(int threads, int ipt) { return prepare_merge_plain<__nv_bfloat16>(threads, ipt); }
+
 }  // namespace lb

@@ -9,4 +9,6 @@ cudaError_t launch_merge_f16(int mode, int threads, int ipt, const MergeArgs &a,
     return dispatch_merge<__half>(mode, threads, ipt, a, s, eb, ea);
 }
 
+cudaError_t prepare_merge_f16(int threads, int ipt) { return prepare_merge_plain<__half>(threads, ipt); }
+
 }  // namespace lb

@@ -9,4 +9,6 @@ cudaError_t launch_merge_f32(int mode, int threads, int ipt, const MergeArgs &a,
     return dispatch_merge<float>(mode, threads, ipt, a, s, eb, ea);
 }
 
+cudaError_t prepare_merge_f32(int threads, int ipt) { return prepare_merge_plain<float>(threads, ipt); }
+
 }  // namespace lb

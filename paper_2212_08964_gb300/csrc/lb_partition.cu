@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
         bool head = false, single = false;
         if (c < G) {
             r = __ldg(carry_row + c);
-            head = r < m && (c == 0 || __ldg(carry_row + c - 1) != r);
+            // Unsigned test: a carry that no tile wrote (a tile that gave up on a bounded wait,
+            // or the -1 fill of a skipped tile) is skipped whatever its value, so y is only
+            // ever written inside [0, m).
+            head = static_cast<unsigned>(r) < static_cast<unsigned>(m) && (c == 0 || __ldg(carry_row + c - 1) != r);
             single = head && (c + 1 >= G || __ldg(carry_row + c + 1) != r);
             if (single) y[r] += __ldg(carry_val + c);
         }

@@ -28,7 +28,7 @@ constexpr int kThreads = 256;  // merge-path launch shape used by this entry poi
 constexpr int kIpt = 8;
 constexpr int kTileItems = LB_SPMV_STATIC_TILE_ITEMS;
 constexpr int kMaxTiles = LB_SPMV_STATIC_MAX_TILES;
-static_assert(kTileItems == kThreads * kIpt - 8, "tile size must match the (256, 8) merge-path shape");
+static_assert(kTileItems == merge_tile_items(kIpt), "tile size must match the (256, 8) merge-path shape");
 
 // Workspace layout, in 4-byte words:
 //   tile_row[kMaxTiles + 1] | tile_nz[kMaxTiles + 1] | carry_row[kMaxTiles] | carry_val[kMaxTiles]
@@ -38,13 +38,15 @@ constexpr size_t kWords = kCarryValWord + kMaxTiles;
 
 }  // namespace
 
-// One copy per device, loaded with this library's module (about 1 MiB).
+// One copy per device, loaded with this library's module (8 MiB).
 static __device__ __align__(256) int g_lb_static_ws[kWords];
 
 namespace {
 
 // Device address of g_lb_static_ws on the current device, looked up once per device (with that
-// device current) and cached; nullptr if the lookup fails.
+// device current) and cached; nullptr if the lookup fails.  The same first call also does the
+// merge-path kernel's host-side set-up for all three value types, so no later call on the
+// device does any.
 int *static_workspace() {
     static int *ptrs[kMaxDevices] = {};
     static std::mutex mu;
@@ -55,6 +57,9 @@ int *static_workspace() {
     if (!ptrs[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_lb_static_ws) != cudaSuccess || !p) return nullptr;
+        if (prepare_merge_f32(kThreads, kIpt) != cudaSuccess || prepare_merge_bf16(kThreads, kIpt) != cudaSuccess ||
+            prepare_merge_f16(kThreads, kIpt) != cudaSuccess)
+            return nullptr;
         ptrs[dev] = static_cast<int *>(p);
     }
     return ptrs[dev];
@@ -72,6 +77,10 @@ extern "C" lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offset
     if (m == 0) return LB_OK;
     if (!row_offsets || !y) return LB_ERR_INVALID_ARG;
     if (nnz > 0 && (!col_idx || !values || !x)) return LB_ERR_INVALID_ARG;
+    const uintptr_t vmask = vdt == LB_F32 ? 3u : 1u;
+    if ((reinterpret_cast<uintptr_t>(col_idx) & 3u) || (reinterpret_cast<uintptr_t>(values) & vmask) ||
+        (reinterpret_cast<uintptr_t>(x) & 3u) || (reinterpret_cast<uintptr_t>(y) & 3u))
+        return LB_ERR_INVALID_ARG;
     const long long work = static_cast<long long>(m) + nnz;
     if (work > static_cast<long long>(kMaxTiles) * kTileItems) return LB_ERR_TOO_LARGE;
     if (nnz == 0) return status_of(cudaMemsetAsync(y, 0, static_cast<size_t>(m) * sizeof(float), stream));
@@ -86,11 +95,10 @@ extern "C" lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offset
     float *carry_val = reinterpret_cast<float *>(ws + kCarryValWord);
 
     // The partition writes every tile boundary and each tile writes its own carry, so nothing
-    // is needed from an earlier call.  The carries are still cleared: a tile that gives up on a
-    // bounded wait (LB_ERR_TIMEOUT in the device error word) then leaves carry (row 0, 0.0),
-    // which adds nothing, instead of a carry left over from an earlier call.
-    cudaError_t e = cudaMemsetAsync(carry_row, 0, static_cast<size_t>(G) * sizeof(int), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(carry_val, 0, static_cast<size_t>(G) * sizeof(float), stream);
+    // is needed from an earlier call.  The carry rows are still filled with -1 first: a tile
+    // that gives up on a bounded wait (LB_ERR_TIMEOUT in the device error word) then leaves a
+    // carry whose row the fixup skips, instead of a carry left over from an earlier call.
+    cudaError_t e = cudaMemsetAsync(carry_row, 0xff, static_cast<size_t>(G) * sizeof(int), stream);
     if (e == cudaSuccess) e = launch_partition(m, nnz, row_offsets, kTileItems, tile_row, tile_nz, stream);
     if (e != cudaSuccess) return status_of(e);
     MergeArgs a{};
@@ -107,5 +115,6 @@ extern "C" lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offset
     a.carry_row = carry_row;
     a.carry_val = carry_val;
     a.err = err;
+    set_merge_alignment(a, vdt == LB_F32 ? 4 : 2);
     return status_of(launch_merge_spmv(vdt, kPlain, kThreads, kIpt, a, stream, nullptr, nullptr));
 }

@@ -50,8 +50,8 @@ LB_ERR_TIMEOUT = -6
 LB_ERR_TOO_LARGE = -7
 # Fixed workspace of lb_spmv_static: tiles of STATIC_TILE_ITEMS work items, at most
 # STATIC_MAX_TILES of them (m + nnz <= STATIC_MAX_TILES * STATIC_TILE_ITEMS).
-STATIC_MAX_TILES = 65536
-STATIC_TILE_ITEMS = 2040
+STATIC_MAX_TILES = 1 << 19
+STATIC_TILE_ITEMS = 248
 
 SCHEDULES = {
     "auto": 0,
@@ -67,6 +67,9 @@ _SCHED_NAMES = {v: k for k, v in SCHEDULES.items()}
 MERGE_SHAPES = [(128, 16), (256, 8), (256, 16), (384, 8), (512, 8)]
 
 _DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+# A plan's tile sets (lb_plan_tiles): block tiles of the passes over the forward partition,
+# warp tiles of the transposed product, warp tiles of the merge-path forward.
+TILE_SETS = {"rows": 0, "transposed": 1, "merge": 2}
 
 
 class LbError(RuntimeError):
@@ -109,6 +112,7 @@ def _declare(lib):
         "lb_plan_create": [_I, _I, _I, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_plan_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
         "lb_plan_partition": [_P, _I, _P, _P, ctypes.POINTER(_I)],
+        "lb_plan_tiles": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)],
         "lb_spmv_planned": [_P, _P, _P, _I, _P, _P, _P],
         "lb_plan_build_transpose": [_P, _P, _P],
         "lb_plan_transpose": [_P, _P, _P, _P],
@@ -182,6 +186,12 @@ def _need(t: torch.Tensor, dtype, name: str, numel: int | None = None):
         raise TypeError(f"{name} must be a torch.Tensor")
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    # The library works on the current device (its workspace, SM count and stream come from
+    # it); a tensor on another device would be read through a foreign address.
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(
+            f"{name} is on cuda:{t.device.index} but the current device is cuda:{torch.cuda.current_device()}"
+        )
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -291,12 +301,22 @@ class Plan:
             "tile_items": ti.value,
         }
 
-    def partition(self, transposed: bool = False):
+    def tiles(self, which: str = "rows") -> tuple[int, int]:
+        """(num_tiles, tile_items) of one tile set: "rows" (the block-level passes), "merge"
+        (the merge-path forward's warp tiles) or "transposed" (the transposed product's)."""
+        g, ti = _I(), _I()
+        _check(_lib.lb_plan_tiles(self._h, TILE_SETS[which], ctypes.byref(g), ctypes.byref(ti)), "lb_plan_tiles")
+        return g.value, ti.value
+
+    def partition(self, transposed: bool = False, which: str | None = None):
+        """Host copy (tile_row, tile_nz) of a tile set: ``which`` as in ``tiles``; by default the
+        "rows" set, or "transposed" with ``transposed=True``."""
+        w = TILE_SETS[which if which is not None else ("transposed" if transposed else "rows")]
         g = _I()
-        _check(_lib.lb_plan_partition(self._h, int(transposed), None, None, ctypes.byref(g)), "lb_plan_partition")
+        _check(_lib.lb_plan_partition(self._h, w, None, None, ctypes.byref(g)), "lb_plan_partition")
         tr = np.empty(g.value + 1, np.int32)
         tn = np.empty(g.value + 1, np.int32)
-        _check(_lib.lb_plan_partition(self._h, int(transposed), tr.ctypes.data, tn.ctypes.data, ctypes.byref(g)), "lb_plan_partition")
+        _check(_lib.lb_plan_partition(self._h, w, tr.ctypes.data, tn.ctypes.data, ctypes.byref(g)), "lb_plan_partition")
         return tr, tn
 
     # -- forward

@@ -40,7 +40,8 @@ def test_transpose_and_its_partition_bit_exact(lb, orc, name):
     oco, ori, operm = orc.transpose(a.row_offsets, a.col_idx, a.n)
     assert np.array_equal(co, oco) and np.array_equal(ri, ori) and np.array_equal(perm, operm)
     tr, tn = plan.partition(transposed=True)
-    otr, otn = orc.partition(oco, plan.info()["tile_items"])
+    assert plan.tiles("transposed")[0] == len(tr) - 1
+    otr, otn = orc.partition(oco, plan.tiles("transposed")[1])
     assert np.array_equal(tr, otr) and np.array_equal(tn, otn)
 
 

@@ -76,3 +76,10 @@ def test_full_size_plan_partition(lb, orc, name):
     otr, otn = orc.partition(a.row_offsets, info["tile_items"])
     assert len(tr) == info["num_tiles"] + 1
     assert np.array_equal(tr, otr) and np.array_equal(tn, otn)
+    # The merge-path forward's warp tiles: the same split at its own tile size.
+    G, T = plan.tiles("merge")
+    assert T == 32 * info["items_per_thread"] - 8
+    wtr, wtn = plan.partition(which="merge")
+    assert len(wtr) == G + 1
+    owtr, owtn = orc.partition(a.row_offsets, T)
+    assert np.array_equal(wtr, owtr) and np.array_equal(wtn, owtn)

@@ -279,16 +279,47 @@ def test_full_size_stencil(lb, orc):
     assert np.array_equal(yi.astype(np.float64), orc.spmv(ai.row_offsets, ai.col_idx, ai.values, xi))
 
 
-@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
-def test_full_size_powerlaw_8m_half(lb, orc, dtype):
+def _tuned_shape(a, dtype_name):
+    """The merge-path shape the shipped autotuner table records for this matrix's class."""
+    from paper_2212_08964_gb300 import autotune
+
+    cfg = autotune.choose(a.row_offsets, autotune.default_table(), dtype_name)
+    if cfg["schedule"] != "merge_path":
+        return None
+    return cfg["threads"], cfg["items_per_thread"]
+
+
+@pytest.mark.parametrize("shape", ["default", "tuned"])
+def test_full_size_powerlaw_8m_f32(lb, orc, shape):
+    """The mixed-precision configuration's FP32-value run (the baseline its BF16/FP16 errors
+    are compared with): 1e-5 * sum|a||x| per row in the default and the tuned launch shape."""
     a = workload("powerlaw_8m")
     x = vec(a.n, 6)
-    y, _ = _run(lb, a, x, "merge_path", dtype)
+    tune = {}
+    if shape == "tuned":
+        ts = _tuned_shape(a, "f32")
+        if ts is not None:
+            tune = {"threads": ts[0], "items_per_thread": ts[1]}
+    y, _ = _run(lb, a, x, "merge_path", torch.float32, **tune)
+    ref, scale = _ref(orc, a, x)
+    mx, med = check_bound(y, ref, scale, TOL32)
+    print(f"powerlaw_8m FP32 ({shape} {tune}): max {mx:.3e} median {med:.3e}")
+    assert lb.device_error() == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("shape", [(256, 8), (128, 16)])
+def test_full_size_powerlaw_8m_half(lb, orc, dtype, shape):
+    """BF16/FP16 values at full size, in the default shape and the narrow-value tuned one."""
+    a = workload("powerlaw_8m")
+    x = vec(a.n, 6)
+    y, _ = _run(lb, a, x, "merge_path", dtype, threads=shape[0], items_per_thread=shape[1])
     ref32, s32 = _ref(orc, a, x)
     mx, med = check_bound(y, ref32, s32, TOL16)
     r16, s16 = _ref(orc, a, x, rounded(a.values, dtype))
-    check_bound(y, r16, s16, TOL32)
-    print(f"powerlaw_8m {dtype}: vs FP32 values max {mx:.3e} median {med:.3e}")
+    mx16, med16 = check_bound(y, r16, s16, TOL32)
+    print(f"powerlaw_8m {dtype} {shape}: vs FP32 values max {mx:.3e} median {med:.3e}; "
+          f"vs rounded values max {mx16:.3e} median {med16:.3e}")
 
 
 @pytest.mark.parametrize("name", ["powerlaw_4k", "stencil", "empty_rows", "few_columns"])

@@ -13,8 +13,10 @@ import torch
 from gpu_helpers import check_bound, dev, to_dev, vec, workload
 from paper_2212_08964_gb300 import synth
 
+from paper_2212_08964_gb300 import lbspmv as _lbspmv
+
 TOL32 = 1e-5
-MAX_WORK = 65536 * 2040  # LB_SPMV_STATIC_MAX_TILES * LB_SPMV_STATIC_TILE_ITEMS
+MAX_WORK = _lbspmv.STATIC_MAX_TILES * _lbspmv.STATIC_TILE_ITEMS  # LB_SPMV_STATIC_MAX_TILES * ..._TILE_ITEMS
 
 
 def _raw_lib():
@@ -104,7 +106,7 @@ def test_static_workspace_reused_across_sizes(lb, orc):
 
 
 @pytest.mark.gpu
-def test_static_at_the_maximum_size(lb):
+def test_static_at_the_maximum_size(lb, orc):
     """m + nnz exactly at the static limit (every workspace tile in use), against lb_spmv."""
     lib = _raw_lib()
     stream = torch.cuda.current_stream().cuda_stream
@@ -125,5 +127,61 @@ def test_static_at_the_maximum_size(lb):
         err = (y.double() - y_ref.double()).abs()
         assert bool((err <= bound).all()), float((err / bound.clamp_min(1e-300)).max())
     assert torch.equal(ys[0], ys[1])
+    # Sampled rows against the oracle itself, one row at a time (first, last and random rows).
+    rows = np.unique(np.concatenate([[0, 1, m - 2, m - 1], np.random.default_rng(81).integers(0, m, 60)]))
+    sel = torch.from_numpy(rows).cuda()
+    cols = ci.view(m, L)[sel].cpu().numpy()
+    vals = v.view(m, L)[sel].cpu().numpy()
+    ro_s = (np.arange(len(rows) + 1) * L).astype(np.int32)
+    xs = x.cpu().numpy()
+    ref = orc.spmv(ro_s, cols.reshape(-1).astype(np.int32), vals.reshape(-1), xs)
+    sc = orc.row_absdot(ro_s, cols.reshape(-1).astype(np.int32), vals.reshape(-1), xs)
+    check_bound(ys[1][sel].cpu().numpy(), ref, sc, TOL32)
     del ci, v
+    _device_error_clear(lb)
+
+
+def _cudart():
+    """The CUDA runtime the library is linked against (already loaded in this process)."""
+    return ctypes.CDLL("libcudart.so.13")
+
+
+# cudaMemPoolAttr values from the CUDA runtime API.
+_POOL_USED_CURRENT = 7
+_POOL_USED_HIGH = 8
+
+
+def _pool_attr(rt, pool, attr):
+    v = ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+    return v.value
+
+
+@pytest.mark.gpu
+def test_static_allocates_nothing(lb):
+    """Two calls after the set-up call leave the device's free memory and the default
+    stream-ordered pool's high-water mark where they were: no cudaMalloc and no
+    cudaMallocAsync (lb_spmv itself takes its workspace from that pool)."""
+    lib = _raw_lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    a = workload("lognormal_1m", 0.3)
+    ro, ci, v = to_dev(a)
+    x = dev(vec(a.n, 82))
+    ys = [torch.empty(a.m, device="cuda") for _ in range(2)]
+    p = lambda t: t.data_ptr()
+    assert lib.lb_spmv_static(a.m, a.n, a.nnz, p(ro), p(ci), p(v), 0, p(x), p(ys[0]), stream) == 0  # set-up
+    torch.cuda.synchronize()
+    rt = _cudart()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, _POOL_USED_HIGH, ctypes.byref(zero)) == 0  # reset to current use
+    used0 = _pool_attr(rt, pool, _POOL_USED_CURRENT)
+    free0 = torch.cuda.mem_get_info()[0]
+    for y in ys:
+        assert lib.lb_spmv_static(a.m, a.n, a.nnz, p(ro), p(ci), p(v), 0, p(x), p(y), stream) == 0
+    torch.cuda.synchronize()
+    assert _pool_attr(rt, pool, _POOL_USED_HIGH) == used0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(ys[0], ys[1])
     _device_error_clear(lb)
