@@ -26,8 +26,10 @@
  *     lb_spmv_planned, lb_spmv_t, lb_spmv_dvalues and lb_spmv_batched allocate nothing and
  *     never synchronize.
  *   - Argument errors are reported before any GPU work as LB_ERR_INVALID_ARG; CUDA errors
- *     as LB_ERR_CUDA.  Kernels never trap: a kernel that gives up on a bounded wait
- *     records LB_ERR_TIMEOUT in a device error word read by lb_device_error().
+ *     as LB_ERR_CUDA.  Pointers must be aligned to their element type.  Kernels never trap
+ *     and never wait on a flag or on other warps or CTAs, so none can hang; a kernel that
+ *     meets a tile only malformed offsets produce skips it and records LB_ERR_BAD_MATRIX in
+ *     a device error word read by lb_device_error().
  *   - Matrix contents are not checked by the SpMV calls; lb_validate_csr checks them.
  *   - No C++ exception crosses this interface.
  */
@@ -47,7 +49,7 @@ typedef enum {
     LB_ERR_UNSUPPORTED = -3, /* valid request this library does not implement */
     LB_ERR_NO_MEMORY = -4,   /* a plan or workspace allocation failed */
     LB_ERR_CUDA = -5,        /* a CUDA runtime call failed */
-    LB_ERR_TIMEOUT = -6,     /* a kernel gave up on a bounded wait (device error word) */
+    LB_ERR_TIMEOUT = -6,     /* reserved: no kernel of this library waits on a signal */
     LB_ERR_TOO_LARGE = -7    /* the request exceeds a fixed-size static workspace */
 } lb_status;
 
@@ -409,9 +411,10 @@ lb_status lb_validate_csr(int m, int n, int nnz, const int *row_offsets, const i
 
 /*
  * Read the current device's error word into *status; clear it when `clear` is nonzero.
- * Synchronizes the device.  LB_OK, or the last error a kernel recorded: LB_ERR_TIMEOUT (a
- * bounded wait gave up) or LB_ERR_BAD_MATRIX (a merge-path tile held more work than a tile
- * can, which only malformed row offsets produce; that tile was skipped).
+ * Synchronizes the device.  LB_OK, or the last error a kernel recorded: LB_ERR_BAD_MATRIX (a
+ * merge-path tile held more work than a tile can, or reached outside the arrays, which only
+ * malformed row offsets produce; that tile was skipped).  LB_ERR_TIMEOUT is reserved: no
+ * kernel of this library waits, so none records it.
  */
 lb_status lb_device_error(int *status, int clear);
 

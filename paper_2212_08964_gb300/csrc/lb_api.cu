@@ -12,7 +12,7 @@
 
 using namespace lb;
 
-// Device error word (per device; kernels that give up on a bounded wait write here).
+// Device error word (per device; a kernel that skips a malformed tile writes here).
 __device__ int g_lb_device_error = 0;
 
 namespace {
@@ -243,7 +243,7 @@ const char *lb_status_string(lb_status s) {
         case LB_ERR_CUDA:
             return "LB_ERR_CUDA: CUDA runtime error";
         case LB_ERR_TIMEOUT:
-            return "LB_ERR_TIMEOUT: a kernel gave up on a bounded wait";
+            return "LB_ERR_TIMEOUT: reserved (no kernel of this library waits)";
         case LB_ERR_TOO_LARGE:
             return "LB_ERR_TOO_LARGE: the matrix exceeds the fixed static workspace";
     }

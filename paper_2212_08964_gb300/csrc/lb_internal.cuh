@@ -1,8 +1,8 @@
-// lb_internal.cuh -- shared device helpers and launcher declarations for liblbspmv.
+// lb_internal.cuh -- shared device helpers and launcher declarations for liblbspmv (sm_103a).
 //
-// Everything here is GB300-specific (sm_103a): 1-D bulk TMA copies (cp.async.bulk) tracked by
-// shared-memory mbarriers, L2 cache-policy hints, and bounded waits that record an error
-// instead of spinning forever.
+// No kernel of the library waits on a flag, a barrier of other warps or another CTA: every
+// warp-tiled kernel runs its warps independently, and the block-level passes use only
+// __syncthreads.  So no kernel can hang on a signal that never comes.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -35,94 +35,13 @@ __device__ __forceinline__ void kbn_add(float &s, float &c, float v) {
 // ------------------------------------------------------------------------------------------
 // PTX wrappers.
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_timer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for an mbarrier phase, giving up after `limit_ns` nanoseconds.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_timer_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > limit_ns) return false;
-    }
-    return true;
-}
-
-// L2 eviction-priority policies for cache hints.
+// L2 eviction-priority policy for cache hints: streamed arrays are marked evict-first so that
+// the gathered vector stays resident in L2.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
-
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// 1-D bulk copy global -> shared, completion counted on `bar` (both addresses 16-byte aligned,
-// bytes a multiple of 16).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
-                                         uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
-        : "memory");
-}
-
-// Orders this thread's generic-proxy shared-memory accesses before later async-proxy (TMA)
-// accesses to the same memory.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Read-only gather with an L2 eviction-priority hint.
-__device__ __forceinline__ float ldg_hint(const float *p, uint64_t policy) {
-    float v;
-    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy));
-    return v;
-}
-
-// Bounded waits give up after this long (the kernel then records LB_ERR_TIMEOUT).
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // ------------------------------------------------------------------------------------------
 // Kernel argument blocks.
@@ -163,9 +82,9 @@ void set_merge_alignment(MergeArgs &a, size_t value_bytes);
 // product gathers its precomputed scaled values this way).
 enum MergeMode { kPlain = 0, kBatched = 1, kGatherSum = 2 };
 
-// Launch the persistent merge-path kernel followed by the fixup kernel.  `grid` <= 0 picks
-// one wave of resident CTAs.  `ev_before` / `ev_after` (may be null) are recorded around the
-// main kernel.
+// Launch the persistent merge-path kernel (one wave of resident CTAs over the warp tiles of
+// `a`, which come from a partition with merge_tile_items(ipt) items per tile) followed by the
+// fixup kernel.  `ev_before` / `ev_after` (may be null) are recorded around the main kernel.
 cudaError_t launch_merge_spmv(lb_dtype vdt, int mode, int threads, int ipt, const MergeArgs &a,
                               cudaStream_t stream, cudaEvent_t ev_before, cudaEvent_t ev_after);
 cudaError_t launch_merge_f32(int mode, int threads, int ipt, const MergeArgs &a, cudaStream_t s,

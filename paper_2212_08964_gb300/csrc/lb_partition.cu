@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
         bool head = false, single = false;
         if (c < G) {
             r = __ldg(carry_row + c);
-            // Unsigned test: a carry that no tile wrote (a tile that gave up on a bounded wait,
-            // or the -1 fill of a skipped tile) is skipped whatever its value, so y is only
-            // ever written inside [0, m).
+            // Unsigned test: a carry row outside [0, m) (the -1 of a skipped malformed tile, or a
+            // value that no tile wrote) is skipped whatever it is, so y is only ever written
+            // inside [0, m).
             head = static_cast<unsigned>(r) < static_cast<unsigned>(m) && (c == 0 || __ldg(carry_row + c - 1) != r);
             single = head && (c + 1 >= G || __ldg(carry_row + c + 1) != r);
             if (single) y[r] += __ldg(carry_val + c);

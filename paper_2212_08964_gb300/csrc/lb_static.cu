@@ -95,9 +95,8 @@ extern "C" lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offset
     float *carry_val = reinterpret_cast<float *>(ws + kCarryValWord);
 
     // The partition writes every tile boundary and each tile writes its own carry, so nothing
-    // is needed from an earlier call.  The carry rows are still filled with -1 first: a tile
-    // that gives up on a bounded wait (LB_ERR_TIMEOUT in the device error word) then leaves a
-    // carry whose row the fixup skips, instead of a carry left over from an earlier call.
+    // is needed from an earlier call.  The carry rows are still filled with -1 first, a row
+    // the fixup skips, so that no carry of an earlier call can ever be added again.
     cudaError_t e = cudaMemsetAsync(carry_row, 0xff, static_cast<size_t>(G) * sizeof(int), stream);
     if (e == cudaSuccess) e = launch_partition(m, nnz, row_offsets, kTileItems, tile_row, tile_nz, stream);
     if (e != cudaSuccess) return status_of(e);

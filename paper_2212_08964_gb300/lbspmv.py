@@ -638,7 +638,7 @@ def validate_csr(row_offsets, col_idx, n: int, check_sorted: bool = True, stream
 
 
 def device_error(clear: bool = True) -> int:
-    """The device error word (0 or LB_ERR_TIMEOUT); synchronizes."""
+    """The device error word (0, or LB_ERR_BAD_MATRIX after a malformed tile); synchronizes."""
     lib = ensure_loaded()
     s = _I()
     _check(lib.lb_device_error(ctypes.byref(s), int(clear)), "lb_device_error")
