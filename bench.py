@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="shrink the workload's m, n and nnz together (small cases for profiler captures)")
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     p.add_argument("--no-secondary", action="store_true",
@@ -249,10 +251,10 @@ def host_cores():
 # ------------------------------------------------------------------------------------------
 
 
-def make_inputs(workload: str):
+def make_inputs(workload: str, scale: float = 1.0):
     from paper_2212_08964_gb300 import synth
 
-    a = synth.workload(workload)
+    a = synth.workload(workload, scale)
     rng = np.random.default_rng(1234)
     x = synth.uniform_pm1(rng, a.n)
     g = synth.uniform_pm1(rng, a.m)
@@ -272,7 +274,7 @@ def run_reference(args, budget_s: float = 150.0):
     rank, world, _ = dist_setup(args)
     if rank != 0:
         return 0
-    a, x, g = make_inputs(args.workload)
+    a, x, g = make_inputs(args.workload, args.scale)
     import oracle
 
     cores = oracle.max_threads()
@@ -296,12 +298,16 @@ def run_reference(args, budget_s: float = 150.0):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps, "warmup": W,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded power-law CSR)",
-        "config": {"workload": f"{args.workload} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz},
+        "config": {"workload": f"{workload_name(args)} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_name(args) -> str:
+    return args.workload if args.scale == 1.0 else f"{args.workload} scaled by {args.scale:g}"
 
 
 def run_ours(args):
@@ -314,7 +320,7 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library is the only compute path)")
     torch.cuda.set_device(local)
     lb.ensure_loaded()
-    a, x, g = make_inputs(args.workload)
+    a, x, g = make_inputs(args.workload, args.scale)
     dev = torch.device("cuda", local)
     ro = torch.from_numpy(a.row_offsets).to(dev)
     ci = torch.from_numpy(a.col_idx).to(dev)
@@ -431,7 +437,7 @@ def run_ours(args):
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded power-law CSR, uniform[-1,1] values, x and g)",
         "config": {
-            "workload": f"{args.workload} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz,
+            "workload": f"{workload_name(args)} fwd+bwd", "m": a.m, "n": a.n, "nnz": a.nnz,
             "schedule": info["schedule"], "threads": info["threads"], "items_per_thread": info["items_per_thread"],
             "num_tiles": info["num_tiles"], "parallelism": f"replicas x{world}",
             "step": "plan built once per structure (partition, CSC view); per step: forward saving x[col], "
@@ -442,7 +448,7 @@ def run_ours(args):
         },
         "roofline": {
             "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": recorded_traffic(args.workload, dom),
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": recorded_traffic(args.workload, dom) if args.scale == 1.0 else None,
             "algorithmic_bytes_per_launch": dom_b, "extra_bytes_per_launch": extra[dom], "avg_launch_ms": dom_ms,
             "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS,
         },
@@ -622,6 +628,14 @@ def run_ours(args):
         sec, steps = oracle_step_time(a, x.astype(np.float64), g.astype(np.float64), a.values.astype(np.float64))
         result["cpu_baseline"] = {"value": total_b / sec / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": f"{steps} full fwd+bwd steps of {args.workload} (FP64 C oracle, OpenMP)"}
+        # The same oracle on one host core, over the leading eighth of the rows (one step).
+        s = row_sample(a, a.m // 8)
+        sec1, _ = oracle_step_time(s, x.astype(np.float64), g[: s.m].astype(np.float64),
+                                   s.values.astype(np.float64), threads=1, max_steps=1)
+        b1 = sum(step_bytes(s.m, s.n, s.nnz))
+        result["cpu_baseline"]["single_thread"] = {
+            "value": b1 / sec1 / 1e9, "unit": UNIT, "cores": 1,
+            "sample": f"one fwd+bwd step over the leading {s.m} rows ({s.nnz} nonzeros) of {args.workload}"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0

@@ -50,7 +50,9 @@ typedef enum {
     LB_ERR_NO_MEMORY = -4,   /* a plan or workspace allocation failed */
     LB_ERR_CUDA = -5,        /* a CUDA runtime call failed */
     LB_ERR_TIMEOUT = -6,     /* reserved: no kernel of this library waits on a signal */
-    LB_ERR_TOO_LARGE = -7    /* the request exceeds a fixed-size static workspace */
+    LB_ERR_TOO_LARGE = -7,   /* the request exceeds a fixed-size static workspace */
+    LB_ERR_OUT_OF_RANGE = -8 /* range-checked build only: an index read from the inputs
+                                (a column, a row, a position) lies outside its array */
 } lb_status;
 
 typedef enum {
@@ -425,6 +427,21 @@ lb_status lb_device_error(int *status, int clear);
  * NULLs to stop.
  */
 lb_status lb_set_profile_events(cudaEvent_t before, cudaEvent_t after);
+
+/*
+ * Test support for the out-of-memory paths (no counterpart in the dissertation; the paper
+ * has no allocation).  Every device allocation the library makes (plan arrays, CSC views,
+ * the workspace of lb_spmv, lb_validate_csr's status word, SSSP's frontier, calibration
+ * buffers) goes through one counter.
+ *   lb_debug_fail_allocations_after(count): the next `count` allocations proceed and every
+ *     later one fails as if the device were full, so the call reports LB_ERR_NO_MEMORY and
+ *     releases what it had allocated; count < 0 removes the limit (the default).
+ *     Process-wide.
+ *   lb_debug_live_allocations(): the library's device allocations currently held (plans not
+ *     yet destroyed, workspaces whose stream-ordered free has not been issued).
+ */
+void lb_debug_fail_allocations_after(int count);
+long long lb_debug_live_allocations(void);
 
 #ifdef __cplusplus
 }

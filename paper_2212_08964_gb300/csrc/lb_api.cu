@@ -2,6 +2,7 @@
 //
 // Host-side only: argument checks, plan objects, schedule selection and kernel dispatch.
 // Every step of the computation runs in this library's kernels.
+#include <atomic>
 #include <climits>
 #include <cstring>
 #include <mutex>
@@ -14,6 +15,54 @@ using namespace lb;
 
 // Device error word (per device; a kernel that skips a malformed tile writes here).
 __device__ int g_lb_device_error = 0;
+
+// ------------------------------------------------------------------------------------------
+// Device allocations: counted, and failed on demand for tests of the out-of-memory paths.
+
+namespace {
+std::atomic<long long> g_live_allocs{0};
+std::atomic<long long> g_alloc_budget{-1};  // allocations left before failures start; -1: no limit
+
+bool take_allocation() {
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) return false;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return true;
+    }
+    return true;
+}
+}  // namespace
+
+namespace lb {
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (!take_allocation()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_allocs;
+    return e;
+}
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (!take_allocation()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) ++g_live_allocs;
+    return e;
+}
+cudaError_t dev_free(void *p) {
+    if (!p) return cudaSuccess;
+    --g_live_allocs;
+    return cudaFree(p);
+}
+cudaError_t dev_free_async(void *p, cudaStream_t st) {
+    if (!p) return cudaSuccess;
+    --g_live_allocs;
+    return cudaFreeAsync(p, st);
+}
+}  // namespace lb
+
+extern "C" void lb_debug_fail_allocations_after(int count) { g_alloc_budget.store(count < 0 ? -1 : count); }
+
+extern "C" long long lb_debug_live_allocations(void) { return g_live_allocs.load(); }
 
 namespace {
 
@@ -134,7 +183,7 @@ template <typename P>
 cudaError_t dmalloc(P **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(P));
+    return dev_malloc(reinterpret_cast<void **>(p), count * sizeof(P));
 }
 
 }  // namespace
@@ -191,12 +240,12 @@ static void release_transpose(lb_plan *p) {
     int **ints[] = {&p->co, &p->ri, &p->perm, &p->t_tile_row, &p->t_tile_nz, &p->t_carry_row, &p->bucket_pos,
                     &p->bucket_perm};
     for (int **q : ints) {
-        if (*q) cudaFree(*q);
+        if (*q) dev_free(*q);
         *q = nullptr;
     }
-    if (p->t_carry_val) cudaFree(p->t_carry_val);
+    if (p->t_carry_val) dev_free(p->t_carry_val);
     p->t_carry_val = nullptr;
-    if (p->pv) cudaFree(p->pv);
+    if (p->pv) dev_free(p->pv);
     p->pv = nullptr;
     p->bucket_shift = 0;
 }
@@ -205,20 +254,20 @@ static void free_plan_arrays(lb_plan *p) {
     release_transpose(p);
     int *nz_ints[] = {p->nz_first, p->nz_last, p->nz_carry_row};
     for (int *q : nz_ints)
-        if (q) cudaFree(q);
-    if (p->nz_carry_val) cudaFree(p->nz_carry_val);
+        if (q) dev_free(q);
+    if (p->nz_carry_val) dev_free(p->nz_carry_val);
     p->nz_first = p->nz_last = p->nz_carry_row = nullptr;
     p->nz_carry_val = nullptr;
-    if (p->mm_carry_row) cudaFree(p->mm_carry_row);
-    if (p->mm_carry_val) cudaFree(p->mm_carry_val);
+    if (p->mm_carry_row) dev_free(p->mm_carry_row);
+    if (p->mm_carry_val) dev_free(p->mm_carry_val);
     p->mm_carry_row = nullptr;
     p->mm_carry_val = nullptr;
     p->mm_cols = 0;
     int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row, p->w_tile_row, p->w_tile_nz, p->w_carry_row};
     for (int *q : ints)
-        if (q) cudaFree(q);
-    if (p->carry_val) cudaFree(p->carry_val);
-    if (p->w_carry_val) cudaFree(p->w_carry_val);
+        if (q) dev_free(q);
+    if (p->carry_val) dev_free(p->carry_val);
+    if (p->w_carry_val) dev_free(p->w_carry_val);
 }
 
 static bool on_device(int dev) {
@@ -246,6 +295,8 @@ const char *lb_status_string(lb_status s) {
             return "LB_ERR_TIMEOUT: reserved (no kernel of this library waits)";
         case LB_ERR_TOO_LARGE:
             return "LB_ERR_TOO_LARGE: the matrix exceeds the fixed static workspace";
+        case LB_ERR_OUT_OF_RANGE:
+            return "LB_ERR_OUT_OF_RANGE: an index read from the inputs lies outside its array (checked build)";
     }
     return "unknown lb_status";
 }
@@ -265,6 +316,7 @@ lb_status lb_set_profile_events(cudaEvent_t before, cudaEvent_t after) {
 
 lb_status lb_partition(int m, int nnz, const int *row_offsets, int tile_items, int *tile_row, int *tile_nz,
                        cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (m < 0 || nnz < 0 || tile_items <= 0 || (m == 0 && nnz != 0)) return LB_ERR_INVALID_ARG;
     if (!row_offsets || !tile_row || !tile_nz) return LB_ERR_INVALID_ARG;
     return from_cuda(launch_partition(m, nnz, row_offsets, tile_items, tile_row, tile_nz, stream));
@@ -272,6 +324,7 @@ lb_status lb_partition(int m, int nnz, const int *row_offsets, int tile_items, i
 
 lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_idx, const void *values,
                   lb_dtype vdt, const float *x, float *y, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!sizes_ok(m, n, nnz) || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
     if (m == 0) return LB_OK;
     if (!row_offsets || !y) return LB_ERR_INVALID_ARG;
@@ -280,7 +333,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
     lb_schedule s;
     lb_tuning t;
     if (!resolve(m, n, nnz, LB_SCHED_AUTO, nullptr, &s, &t)) return LB_ERR_INVALID_ARG;
-    if (s != LB_SCHED_MERGE_PATH) return from_cuda(launch_mapped(s, t, vdt, m, row_offsets, col_idx, values, x, y, stream));
+    if (s != LB_SCHED_MERGE_PATH) return from_cuda(launch_mapped(s, t, vdt, m, n, nnz, row_offsets, col_idx, values, x, y, stream));
     if (!aligned(col_idx, 4) || !aligned(values, value_bytes(vdt)) || !aligned(x, 4) || !aligned(y, 4))
         return LB_ERR_INVALID_ARG;
     int *err = device_error_word();
@@ -291,7 +344,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
     const size_t bytes = (2 * (static_cast<size_t>(G) + 1) + static_cast<size_t>(G)) * sizeof(int) +
                          static_cast<size_t>(G) * sizeof(float);
     void *ws = nullptr;
-    cudaError_t e = cudaMallocAsync(&ws, bytes, stream);
+    cudaError_t e = dev_malloc_async(&ws, bytes, stream);
     if (e != cudaSuccess) return from_cuda(e);
     int *tile_row = static_cast<int *>(ws);
     int *tile_nz = tile_row + G + 1;
@@ -309,6 +362,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
         a.idx = col_idx;
         a.val = values;
         a.x = x;
+        a.x_len = n;
         a.y = y;
         a.carry_row = carry_row;
         a.carry_val = carry_val;
@@ -316,7 +370,7 @@ lb_status lb_spmv(int m, int n, int nnz, const int *row_offsets, const int *col_
         set_merge_alignment(a, value_bytes(vdt));
         e = launch_merge_spmv(vdt, kPlain, t.threads, t.items_per_thread, a, stream, g_ev_before, g_ev_after);
     }
-    cudaError_t e2 = cudaFreeAsync(ws, stream);
+    cudaError_t e2 = dev_free_async(ws, stream);
     return from_cuda(e != cudaSuccess ? e : e2);
 }
 
@@ -337,6 +391,7 @@ static lb_status planned_forward(const lb_plan *p, const int *col_idx, const voi
     a.idx = col_idx;
     a.val = values;
     a.x = x;
+    a.x_len = p->n;
     a.y = y;
     a.carry_row = p->w_carry_row;
     a.carry_val = p->w_carry_val;
@@ -349,6 +404,7 @@ static lb_status planned_forward(const lb_plan *p, const int *col_idx, const voi
 
 lb_status lb_plan_create(int m, int n, int nnz, const int *row_offsets, lb_schedule s, const lb_tuning *t,
                          cudaStream_t stream, lb_plan **out) {
+    LB_NVTX_RANGE();
     if (!out) return LB_ERR_INVALID_ARG;
     *out = nullptr;
     if (!sizes_ok(m, n, nnz) || !sched_ok(s)) return LB_ERR_INVALID_ARG;
@@ -471,6 +527,7 @@ lb_status lb_plan_partition(const lb_plan *p, int which, int *tile_row, int *til
 
 lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, const float *x,
                           float *y, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
     if (p->m == 0) return LB_OK;
     if (!y || (p->nnz > 0 && (!col_idx || !values || !x))) return LB_ERR_INVALID_ARG;
@@ -480,12 +537,13 @@ lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *valu
         return from_cuda(launch_nzsplit(vdt, p->G_nz, p->m, p->nnz, p->nz_first, p->nz_last, p->ro, col_idx, values, x,
                                         y, p->nz_carry_row, p->nz_carry_val, stream));
     if (p->sched != LB_SCHED_MERGE_PATH)
-        return from_cuda(launch_mapped(p->sched, p->tune, vdt, p->m, p->ro, col_idx, values, x, y, stream));
+        return from_cuda(launch_mapped(p->sched, p->tune, vdt, p->m, p->n, p->nnz, p->ro, col_idx, values, x, y, stream));
     return planned_forward(p, col_idx, values, vdt, x, y, nullptr, stream);
 }
 
 lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
                                const float *x, float *y, float *x_gathered, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
     if (p->sched != LB_SCHED_MERGE_PATH) return LB_ERR_UNSUPPORTED;
     if (p->m == 0) return LB_OK;
@@ -497,6 +555,7 @@ lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void 
 }
 
 lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p) return LB_ERR_INVALID_ARG;
     if (p->nnz > 0 && !col_idx) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
@@ -507,12 +566,12 @@ lb_status lb_plan_build_transpose(lb_plan *p, const int *col_idx, cudaStream_t s
     // transpose is built once per structure).
     {
         int *d_status = nullptr, h_status = 0;
-        if ((e = cudaMallocAsync(reinterpret_cast<void **>(&d_status), sizeof(int), stream)) != cudaSuccess)
+        if ((e = dev_malloc_async(reinterpret_cast<void **>(&d_status), sizeof(int), stream)) != cudaSuccess)
             return from_cuda(e);
         e = launch_validate(p->m, n, nnz, p->ro, col_idx, 0, d_status, stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
-        cudaFreeAsync(d_status, stream);
+        dev_free_async(d_status, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return from_cuda(e);
         if (h_status != 0) return LB_ERR_BAD_MATRIX;
@@ -589,6 +648,7 @@ static lb_status transposed_product(const lb_plan *p, const void *values, lb_dty
     a.row_end = p->co + 1;
     a.idx = p->bucket_shift > 0 ? p->bucket_perm : p->perm;
     a.x = p->pv;
+    a.x_len = p->nnz;
     a.y = dx;
     a.carry_row = p->t_carry_row;
     a.carry_val = p->t_carry_val;
@@ -602,6 +662,7 @@ static lb_status transposed_product(const lb_plan *p, const void *values, lb_dty
 
 lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const float *g, float *dx,
                     cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !p->has_t || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
     if (p->n == 0) return LB_OK;
     if (!dx || (p->nnz > 0 && (!values || !g))) return LB_ERR_INVALID_ARG;
@@ -612,6 +673,7 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
 
 lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
                            const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !p->has_t || !dtype_ok(vdt) || !dx || !dvalues) return LB_ERR_INVALID_ARG;
     if (p->nnz > 0 && (!values || !g || !x_gathered)) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
@@ -623,29 +685,32 @@ lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, c
 lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
                                    const float *g, const float *x_gathered, float *dx, float *dvalues,
                                    cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !dtype_ok(vdt) || !dx) return LB_ERR_INVALID_ARG;
     if (p->nnz > 0 && (!col_idx || !values || !g || (dvalues && !x_gathered))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->n == 0) return LB_OK;
     cudaError_t e = cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream);
     if (e != cudaSuccess || p->nnz == 0) return from_cuda(e);
-    return from_cuda(launch_csr_backward_scatter(vdt, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row,
+    return from_cuda(launch_csr_backward_scatter(vdt, p->wG, p->w_tile_items, p->m, p->n, p->nnz, p->w_tile_row,
                                                  p->w_tile_nz, p->ro + 1, g, values, col_idx, dx, x_gathered, dvalues,
                                                  stream));
 }
 
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
                           cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return LB_OK;
     if (!col_idx || !g || !x || !dvalues) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     return from_cuda(
-        launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, dvalues, stream));
+        launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, p->n, dvalues, stream));
 }
 
 lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
                                    cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return LB_OK;
     if (!g || !x_gathered || !dvalues) return LB_ERR_INVALID_ARG;
@@ -656,6 +721,7 @@ lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float
 
 lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, int kc, const float *B,
                           float *C, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !dtype_ok(vdt) || kc < 0) return LB_ERR_INVALID_ARG;
     if (p->m == 0 || kc == 0) return LB_OK;
     if (!C || (p->nnz > 0 && (!col_idx || !values || !B))) return LB_ERR_INVALID_ARG;
@@ -665,8 +731,8 @@ lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb
     if (p->tile_items > 2048) return LB_ERR_UNSUPPORTED;  // SpMM stages tiles of up to 2048 items
     if (kc > p->mm_cols) {
         // Carries for G tiles of kc columns; allocated once per plan and column count growth.
-        if (p->mm_carry_row) cudaFree(p->mm_carry_row);
-        if (p->mm_carry_val) cudaFree(p->mm_carry_val);
+        if (p->mm_carry_row) dev_free(p->mm_carry_row);
+        if (p->mm_carry_val) dev_free(p->mm_carry_val);
         p->mm_carry_row = nullptr;
         p->mm_carry_val = nullptr;
         p->mm_cols = 0;
@@ -688,6 +754,7 @@ void lb_plan_destroy(lb_plan *p) {
 lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, const int *h_nnz,
                                  const int *row_offsets_concat, lb_schedule s, const lb_tuning *t,
                                  cudaStream_t stream, lb_batched_plan **out) {
+    LB_NVTX_RANGE();
     if (!out) return LB_ERR_INVALID_ARG;
     *out = nullptr;
     if (count < 0 || (count > 0 && (!h_m || !h_n || !h_nnz))) return LB_ERR_INVALID_ARG;
@@ -730,8 +797,8 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     int *d_ro_pos = nullptr, *d_row_base = nullptr;
     cudaError_t e = cudaSuccess;
     auto fail = [&](cudaError_t err) {
-        if (d_ro_pos) cudaFree(d_ro_pos);
-        if (d_row_base) cudaFree(d_row_base);
+        if (d_ro_pos) dev_free(d_ro_pos);
+        if (d_row_base) dev_free(d_row_base);
         lb_batched_plan_destroy(p);
         return from_cuda(err);
     };
@@ -753,8 +820,8 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_nz, &zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_mat, &zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(e);
-        cudaFree(d_ro_pos);
-        cudaFree(d_row_base);
+        dev_free(d_ro_pos);
+        dev_free(d_row_base);
         *out = p;
         return LB_OK;
     }
@@ -772,8 +839,8 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     if (e == cudaSuccess) e = launch_tile_matrix(p->G, p->tile_nz, kc, p->mat_nz_base, p->tile_mat, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the index scratch is freed below
     if (e != cudaSuccess) return fail(e);
-    cudaFree(d_ro_pos);
-    cudaFree(d_row_base);
+    dev_free(d_ro_pos);
+    dev_free(d_row_base);
     *out = p;
     return LB_OK;
 }
@@ -800,6 +867,7 @@ lb_status lb_batched_plan_partition(const lb_batched_plan *p, int *tile_row, int
 
 lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, const void *values_concat,
                           lb_dtype vdt, const float *x_concat, float *y_concat, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!p || !dtype_ok(vdt)) return LB_ERR_INVALID_ARG;
     if (p->total_rows == 0) return LB_OK;
     if (!y_concat || (p->total_nnz > 0 && (!col_idx_concat || !values_concat || !x_concat)))
@@ -822,6 +890,7 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, c
     a.idx = col_idx_concat;
     a.val = values_concat;
     a.x = x_concat;
+    a.x_len = p->total_cols;
     a.y = y_concat;
     a.carry_row = p->carry_row;
     a.carry_val = p->carry_val;
@@ -838,13 +907,14 @@ void lb_batched_plan_destroy(lb_batched_plan *p) {
     if (!p) return;
     int *ints[] = {p->ro_g, p->mat_nz_base, p->mat_col_base, p->tile_row, p->tile_nz, p->tile_mat, p->carry_row};
     for (int *q : ints)
-        if (q) cudaFree(q);
-    if (p->carry_val) cudaFree(p->carry_val);
+        if (q) dev_free(q);
+    if (p->carry_val) dev_free(p->carry_val);
     delete p;
 }
 
 lb_status lb_sssp(int n, int nnz, const int *row_offsets, const int *col_idx, const float *weights, int source,
                   float *dist, int *iterations, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (n <= 0 || nnz < 0 || source < 0 || source >= n || !row_offsets || !dist || !iterations) return LB_ERR_INVALID_ARG;
     if (nnz > 0 && !col_idx) return LB_ERR_INVALID_ARG;
     return from_cuda(run_sssp(n, nnz, row_offsets, col_idx, weights, source, dist, iterations, stream));
@@ -852,6 +922,7 @@ lb_status lb_sssp(int n, int nnz, const int *row_offsets, const int *col_idx, co
 
 lb_status lb_coo_row_offsets(int m, int nnz, const int *row_idx, int *row_offsets, int *d_status,
                              cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (m < 0 || nnz < 0 || (m == 0 && nnz != 0) || !row_offsets || !d_status || (nnz > 0 && !row_idx))
         return LB_ERR_INVALID_ARG;
     return from_cuda(launch_coo_offsets(m, nnz, row_idx, row_offsets, d_status, stream));
@@ -859,6 +930,7 @@ lb_status lb_coo_row_offsets(int m, int nnz, const int *row_idx, int *row_offset
 
 lb_status lb_validate_csr(int m, int n, int nnz, const int *row_offsets, const int *col_idx, int check_sorted,
                           int *d_status, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!sizes_ok(m, n, nnz) || !d_status || !row_offsets || (nnz > 0 && !col_idx)) return LB_ERR_INVALID_ARG;
     return from_cuda(launch_validate(m, n, nnz, row_offsets, col_idx, check_sorted, d_status, stream));
 }

@@ -19,8 +19,8 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                                                             const int *__restrict__ tile_nz,
                                                             const int *__restrict__ row_end,
                                                             const int *__restrict__ ci, const float *__restrict__ g,
-                                                            const float *__restrict__ x, float *__restrict__ dv,
-                                                            int *__restrict__ rowid) {
+                                                            const float *__restrict__ x, int n,
+                                                            float *__restrict__ dv, int *__restrict__ rowid) {
     constexpr int T = THREADS * IPT;
     __shared__ int s_re[T];
     __shared__ int s_row[T];
@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                 const int row = r0 + s_row[j];
                 if (ROWID)
                     rowid[k] = row;
-                else
-                    dv[k] = __ldg(g + row) * __ldg(x + __ldg(ci + k));
+                else {
+                    const int c = __ldg(ci + k);
+                    dv[k] = LB_IN_RANGE(c, n) ? __ldg(g + row) * __ldg(x + c) : 0.f;
+                }
             }
         }
         __syncthreads();
@@ -70,19 +72,19 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
 
 template <bool ROWID>
 static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, const int *tile_nz,
-                                    const int *row_end, const int *ci, const float *g, const float *x, float *dv,
-                                    int *rowid, cudaStream_t st) {
+                                    const int *row_end, const int *ci, const float *g, const float *x, int n,
+                                    float *dv, int *rowid, cudaStream_t st) {
     if (G <= 0) return cudaSuccess;
     int grid = G;
     const int cap = current_sm_count() * 6;
     if (grid > cap) grid = cap;
     // The staged row ends must fit: a tile holds at most tile_items rows.
     if (tile_items <= 1024)
-        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
+        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
     else if (tile_items <= 2048)
-        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
+        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
     else if (tile_items <= 4096)
-        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, dv, rowid);
+        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -102,7 +104,7 @@ static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, 
 // warp's shared memory in a lane-consecutive pass, so that the bucket positions of
 // neighbouring nonzeros (consecutive inside a bucket) coalesce.
 struct CsrBackwardArgs {
-    int G, m, nnz;
+    int G, m, nnz, n;  // n: columns (dx entries), checked against in the range-checked build
     const int *tile_row, *tile_nz, *row_end;
     const float *g;
     const void *values;
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(256) csr_backward_kernel(const CsrBackwardArgs
         if (SCATTER) {
 #pragma unroll
             for (int q = 0; q < IPT; ++q)
-                if ((vm >> q) & 1u) atomicAdd(a.dx + cc[q], vv[q] * gq[q]);
+                if (((vm >> q) & 1u) && LB_IN_RANGE(cc[q], a.n)) atomicAdd(a.dx + cc[q], vv[q] * gq[q]);
         }
         if (want_pv) {
 #pragma unroll
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(256) csr_backward_kernel(const CsrBackwardArgs
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 const int j = 32 * q + lane;
-                if (j >= lead && j < lead + nk) a.pv[bp[q]] = buf[ppad(j)];
+                if (j >= lead && j < lead + nk && LB_IN_RANGE(bp[q], a.nnz)) a.pv[bp[q]] = buf[ppad(j)];
             }
         }
         __syncwarp();  // the counts and the buffer are reused by the next tile
@@ -344,7 +346,7 @@ cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int tile_items, int
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz,
+cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int n, int nnz,
                                         const int *tile_row,
                                         const int *tile_nz, const int *row_end, const float *g, const void *values,
                                         const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream) {
@@ -354,7 +356,7 @@ cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_it
     CsrBackwardArgs a{};
     a.G = num_tiles, a.m = m, a.nnz = nnz;
     a.tile_row = tile_row, a.tile_nz = tile_nz, a.row_end = row_end, a.g = g, a.values = values;
-    a.xg = xg, a.dv = dv, a.ci = ci, a.dx = dx;
+    a.xg = xg, a.dv = dv, a.ci = ci, a.dx = dx, a.n = n;
     switch (vdt) {
         case LB_F32:
             return launch_csr_backward_t<float, true>(a, tile_items, stream);
@@ -367,14 +369,15 @@ cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_it
 }
 
 cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
+                           const int *row_end, const int *ci, const float *g, const float *x, int n, float *dv,
                            cudaStream_t stream) {
-    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, dv, nullptr, stream);
+    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, n, dv, nullptr,
+                                   stream);
 }
 
 cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
                                 const int *row_end, int *rowid, cudaStream_t stream) {
-    return launch_tile_rows<true>(num_tiles, tile_items, tile_row, tile_nz, row_end, nullptr, nullptr, nullptr,
+    return launch_tile_rows<true>(num_tiles, tile_items, tile_row, tile_nz, row_end, nullptr, nullptr, nullptr, 0,
                                   nullptr, rowid, stream);
 }
 

@@ -82,15 +82,16 @@ cudaError_t best_of(int reps, cudaStream_t st, F launch, float *best_ms) {
 }  // namespace
 
 extern "C" lb_status lb_calibrate(lb_calibration *out, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!out) return LB_ERR_INVALID_ARG;
     const long long kBuf = 1ll << 28;       // 256M floats = 1 GiB per buffer
     const long long kVec = 1ll << 22;       // 4M floats = 16 MB gathered vector
     const long long kGathers = 1ll << 26;   // 64M gathers
     float *a = nullptr, *b = nullptr, *x = nullptr, *sink = nullptr;
-    cudaError_t e = cudaMalloc(&a, kBuf * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&b, kBuf * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&x, kVec * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
+    cudaError_t e = lb::dev_malloc(&a, kBuf * sizeof(float));
+    if (e == cudaSuccess) e = lb::dev_malloc(&b, kBuf * sizeof(float));
+    if (e == cudaSuccess) e = lb::dev_malloc(&x, kVec * sizeof(float));
+    if (e == cudaSuccess) e = lb::dev_malloc(&sink, sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, kBuf * sizeof(float), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, kVec * sizeof(float), stream);
     const int sms = lb::current_sm_count();
@@ -113,9 +114,9 @@ extern "C" lb_status lb_calibrate(lb_calibration *out, cudaStream_t stream) {
         out->read_GBps = static_cast<double>(kBuf) * sizeof(float) / (ms_r * 1e-3) / 1e9;
         out->copy_GBps = 2.0 * static_cast<double>(kBuf / 2) * sizeof(float) / (ms_c * 1e-3) / 1e9;
     }
-    if (a) cudaFree(a);
-    if (b) cudaFree(b);
-    if (x) cudaFree(x);
-    if (sink) cudaFree(sink);
+    if (a) lb::dev_free(a);
+    if (b) lb::dev_free(b);
+    if (x) lb::dev_free(x);
+    if (sink) lb::dev_free(sink);
     return e == cudaSuccess ? LB_OK : (e == cudaErrorMemoryAllocation ? LB_ERR_NO_MEMORY : LB_ERR_CUDA);
 }

@@ -76,7 +76,7 @@ cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *
     const long long scratch = scan_scratch_ints(static_cast<long long>(n) + 1);
     const size_t ints = 4 * (static_cast<size_t>(n) + 1) + static_cast<size_t>(scratch) + 1;
     int *work = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&work), ints * sizeof(int), st);
+    cudaError_t e = dev_malloc_async(reinterpret_cast<void **>(&work), ints * sizeof(int), st);
     if (e != cudaSuccess) return e;
     int *f_cur = work;
     int *f_next = f_cur + n + 1;
@@ -118,7 +118,7 @@ cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *
     }
     (void)nnz;
     if (h_count) cudaFreeHost(h_count);
-    cudaError_t e2 = cudaFreeAsync(work, st);
+    cudaError_t e2 = dev_free_async(work, st);
     return e != cudaSuccess ? e : e2;
 }
 

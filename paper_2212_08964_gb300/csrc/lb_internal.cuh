@@ -12,7 +12,29 @@
 
 #include "lbspmv.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lb {
+
+// ------------------------------------------------------------------------------------------
+// Range checks.  In the range-checked build (LB_CHECKED, liblbspmv_checked.so) every index a
+// kernel reads from its inputs (a column, a row, a position) is tested against the array it
+// addresses before the access; a violation skips the access and records LB_ERR_OUT_OF_RANGE
+// in the device error word.  The build stands in for a memory checker.  In the normal build
+// the tests compile away and the inputs are trusted (lb_validate_csr checks them).
+#ifdef LB_CHECKED
+}  // namespace lb
+extern __device__ int g_lb_device_error;
+namespace lb {
+__device__ __forceinline__ bool in_range(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicExch(&g_lb_device_error, static_cast<int>(LB_ERR_OUT_OF_RANGE));
+    return false;
+}
+#define LB_IN_RANGE(i, n) ::lb::in_range((i), (n))
+#else
+#define LB_IN_RANGE(i, n) true
+#endif
 
 // ------------------------------------------------------------------------------------------
 // Value types: stored as FP32, BF16 or FP16, always widened to FP32 in registers.
@@ -58,6 +80,7 @@ struct MergeArgs {
     const int *idx;       // gather index per atom (column index; CSC row index when transposed)
     const void *val;      // values, per atom (unused by the gather-sum product)
     const float *x;       // gathered dense vector
+    long long x_len;      // its length (the range-checked build tests every gather against it)
     float *y;             // output, one entry per row
     int *carry_row;       // [G] row left open at the end of each tile
     float *carry_val;     // [G] that row's partial sum inside the tile
@@ -109,12 +132,12 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
                              int *tile_nz, cudaStream_t stream);
 
 // Thread-, group- and block-mapped schedules.
-cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, const int *ro,
+cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, int n, int nnz, const int *ro,
                           const int *ci, const void *v, const float *x, float *y, cudaStream_t stream);
 
 // dvalues over the forward block tiles, gathering x: dv[k] = g[row(k)] * x[ci[k]].
 cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, float *dv,
+                           const int *row_end, const int *ci, const float *g, const float *x, int n, float *dv,
                            cudaStream_t stream);
 
 // Stable CSR -> CSC transpose (deterministic LSD radix sort by column).
@@ -147,7 +170,7 @@ cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_r
                                 const int *row_end, int *rowid, cudaStream_t stream);
 // The same pass adding v[k] * g[row(k)] into dx[col_idx[k]] with float reductions (dx zeroed
 // by the caller; not bit-reproducible), and dv[k] = g[row(k)] * xg[k] when dv is given.
-cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz,
+cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int n, int nnz,
                                         const int *tile_row,
                                         const int *tile_nz, const int *row_end, const float *g, const void *values,
                                         const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream);
@@ -193,6 +216,32 @@ long long scan_scratch_ints(long long n);
 
 // Device properties of the current device (cached).
 int current_sm_count();
+
+// An NVTX range around a public call, named after it: visible on profiler timelines, and
+// nearly free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define LB_NVTX_RANGE() ::lb::NvtxRange lb_nvtx_range_(__func__)
+
+// Every device allocation of the library goes through these four calls.  They count the live
+// allocations and, for tests of the out-of-memory paths, fail on demand as if the device
+// were full (lb_debug_fail_allocations_after in the C ABI).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+cudaError_t dev_free(void *p);
+cudaError_t dev_free_async(void *p, cudaStream_t st);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st) {
+    return dev_malloc_async(reinterpret_cast<void **>(p), bytes, st);
+}
 
 // Device address of the current device's error word (looked up once per device), or nullptr.
 int *device_error_ptr();

@@ -19,21 +19,30 @@
 
 namespace lb {
 
+// v[k] * x[ci[k]] for nonzero k (tested against nnz and n in the range-checked build).
 template <typename V>
-__global__ void __launch_bounds__(256) thread_mapped_kernel(int m, const int *__restrict__ ro,
+__device__ __forceinline__ float nz_product(const V *__restrict__ v, const int *__restrict__ ci,
+                                           const float *__restrict__ x, long long k, int nnz, int n) {
+    if (!LB_IN_RANGE(k, nnz)) return 0.f;
+    const int c = __ldg(ci + k);
+    return LB_IN_RANGE(c, n) ? to_f32(__ldg(v + k)) * __ldg(x + c) : 0.f;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) thread_mapped_kernel(int m, int n, int nnz, const int *__restrict__ ro,
                                                             const int *__restrict__ ci, const V *__restrict__ v,
                                                             const float *__restrict__ x, float *__restrict__ y) {
     for (long long row = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; row < m;
          row += static_cast<long long>(gridDim.x) * blockDim.x) {
         float s = 0.f, c = 0.f;
         const int e = __ldg(ro + row + 1);
-        for (int k = __ldg(ro + row); k < e; ++k) kbn_add(s, c, to_f32(__ldg(v + k)) * __ldg(x + __ldg(ci + k)));
+        for (int k = __ldg(ro + row); k < e; ++k) kbn_add(s, c, nz_product(v, ci, x, k, nnz, n));
         y[row] = s + c;
     }
 }
 
 template <typename V, int G>
-__global__ void __launch_bounds__(256) group_mapped_kernel(int m, const int *__restrict__ ro,
+__global__ void __launch_bounds__(256) group_mapped_kernel(int m, int n, int nnz, const int *__restrict__ ro,
                                                            const int *__restrict__ ci, const V *__restrict__ v,
                                                            const float *__restrict__ x, float *__restrict__ y) {
     static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "group size");
@@ -73,7 +82,7 @@ __global__ void __launch_bounds__(256) group_mapped_kernel(int m, const int *__r
             float p = 0.f;
             if (k < total) {
                 const int nz = base + k;
-                p = to_f32(__ldg(v + nz)) * __ldg(x + __ldg(ci + nz));
+                p = nz_product(v, ci, x, nz, nnz, n);
             }
             // Segmented inclusive scan of the round's products by row.
             float sp = p;
@@ -96,7 +105,7 @@ __global__ void __launch_bounds__(256) group_mapped_kernel(int m, const int *__r
 
 // Block-mapped: the group is the whole block (THREADS rows per block, shared-memory scans).
 template <typename V, int THREADS>
-__global__ void __launch_bounds__(THREADS) block_mapped_kernel(int m, const int *__restrict__ ro,
+__global__ void __launch_bounds__(THREADS) block_mapped_kernel(int m, int n, int nnz, const int *__restrict__ ro,
                                                                const int *__restrict__ ci, const V *__restrict__ v,
                                                                const float *__restrict__ x, float *__restrict__ y) {
     constexpr int WARPS = THREADS / 32;
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(THREADS) block_mapped_kernel(int m, const int 
             float p = 0.f;
             if (k < total) {
                 const int nz = base + k;
-                p = to_f32(__ldg(v + nz)) * __ldg(x + __ldg(ci + nz));
+                p = nz_product(v, ci, x, nz, nnz, n);
             }
             // Segmented inclusive scan over the block: (starts a row segment?, value).
             const int rprev = __shfl_up_sync(0xffffffffu, rl, 1);
@@ -192,13 +201,13 @@ __global__ void __launch_bounds__(THREADS) block_mapped_kernel(int m, const int 
 }
 
 template <typename V>
-static cudaError_t launch_mapped_t(lb_schedule s, const lb_tuning &t, int m, const int *ro, const int *ci,
+static cudaError_t launch_mapped_t(lb_schedule s, const lb_tuning &t, int m, int n, int nnz, const int *ro, const int *ci,
                                    const V *v, const float *x, float *y, cudaStream_t st) {
     const int sms = current_sm_count();
     if (s == LB_SCHED_THREAD_MAPPED) {
         long long blocks = (static_cast<long long>(m) + 255) / 256;
         if (blocks > static_cast<long long>(sms) * 64) blocks = static_cast<long long>(sms) * 64;
-        thread_mapped_kernel<V><<<static_cast<int>(blocks), 256, 0, st>>>(m, ro, ci, v, x, y);
+        thread_mapped_kernel<V><<<static_cast<int>(blocks), 256, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
         return cudaGetLastError();
     }
     if (s == LB_SCHED_BLOCK_MAPPED) {
@@ -206,9 +215,9 @@ static cudaError_t launch_mapped_t(lb_schedule s, const lb_tuning &t, int m, con
         long long blocks = (static_cast<long long>(m) + th - 1) / th;
         if (blocks > static_cast<long long>(sms) * 32) blocks = static_cast<long long>(sms) * 32;
         if (th == 128)
-            block_mapped_kernel<V, 128><<<static_cast<int>(blocks), 128, 0, st>>>(m, ro, ci, v, x, y);
+            block_mapped_kernel<V, 128><<<static_cast<int>(blocks), 128, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
         else if (th == 256)
-            block_mapped_kernel<V, 256><<<static_cast<int>(blocks), 256, 0, st>>>(m, ro, ci, v, x, y);
+            block_mapped_kernel<V, 256><<<static_cast<int>(blocks), 256, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
         else
             return cudaErrorInvalidValue;
         return cudaGetLastError();
@@ -218,16 +227,16 @@ static cudaError_t launch_mapped_t(lb_schedule s, const lb_tuning &t, int m, con
     if (blocks > static_cast<long long>(sms) * 64) blocks = static_cast<long long>(sms) * 64;
     switch (g) {
         case 4:
-            group_mapped_kernel<V, 4><<<static_cast<int>(blocks), 256, 0, st>>>(m, ro, ci, v, x, y);
+            group_mapped_kernel<V, 4><<<static_cast<int>(blocks), 256, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
             break;
         case 8:
-            group_mapped_kernel<V, 8><<<static_cast<int>(blocks), 256, 0, st>>>(m, ro, ci, v, x, y);
+            group_mapped_kernel<V, 8><<<static_cast<int>(blocks), 256, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
             break;
         case 16:
-            group_mapped_kernel<V, 16><<<static_cast<int>(blocks), 256, 0, st>>>(m, ro, ci, v, x, y);
+            group_mapped_kernel<V, 16><<<static_cast<int>(blocks), 256, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
             break;
         case 32:
-            group_mapped_kernel<V, 32><<<static_cast<int>(blocks), 256, 0, st>>>(m, ro, ci, v, x, y);
+            group_mapped_kernel<V, 32><<<static_cast<int>(blocks), 256, 0, st>>>(m, n, nnz, ro, ci, v, x, y);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -235,17 +244,17 @@ static cudaError_t launch_mapped_t(lb_schedule s, const lb_tuning &t, int m, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, const int *ro, const int *ci,
+cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, int n, int nnz, const int *ro, const int *ci,
                           const void *v, const float *x, float *y, cudaStream_t stream) {
     if (m <= 0) return cudaSuccess;
     switch (vdt) {
         case LB_F32:
-            return launch_mapped_t<float>(s, t, m, ro, ci, static_cast<const float *>(v), x, y, stream);
+            return launch_mapped_t<float>(s, t, m, n, nnz, ro, ci, static_cast<const float *>(v), x, y, stream);
         case LB_BF16:
-            return launch_mapped_t<__nv_bfloat16>(s, t, m, ro, ci, static_cast<const __nv_bfloat16 *>(v), x, y,
+            return launch_mapped_t<__nv_bfloat16>(s, t, m, n, nnz, ro, ci, static_cast<const __nv_bfloat16 *>(v), x, y,
                                                   stream);
         case LB_F16:
-            return launch_mapped_t<__half>(s, t, m, ro, ci, static_cast<const __half *>(v), x, y, stream);
+            return launch_mapped_t<__half>(s, t, m, n, nnz, ro, ci, static_cast<const __half *>(v), x, y, stream);
     }
     return cudaErrorInvalidValue;
 }

@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
         // 1. This tile's gathers.
         float xv[IPT];
 #pragma unroll
-        for (int q = 0; q < IPT; ++q) xv[q] = ((vm >> q) & 1u) ? __ldg(a.x + col[q]) : 0.f;
+        for (int q = 0; q < IPT; ++q)
+            xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) ? __ldg(a.x + col[q]) : 0.f;
 
         // 2. The next tile's indices (and the bounds of the one after) while they are in flight.
         const bool has_next = t + nw < G;
@@ -313,16 +314,16 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
 #pragma unroll
         for (int q = 1; q < IPT; ++q)
             if (!((f >> q) & 1u)) p[q] += p[q - 1];
+        // Across lanes: lane L's last segment began in lane seg, the last lane at or before L
+        // holding a row start (lane 0 if none), and a step adds lane L - off's partial sum
+        // only while that lane lies in the same segment.
         float v = p[IPT - 1];
-        int hf = f != 0u;
+        const uint32_t starts = __ballot_sync(0xffffffffu, f != 0u) & (0xffffffffu >> (31 - lane));
+        const int seg = starts ? 31 - __clz(starts) : 0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const float vu = __shfl_up_sync(0xffffffffu, v, off);
-            const int fu = __shfl_up_sync(0xffffffffu, hf, off);
-            if (lane >= off) {
-                if (!hf) v += vu;
-                hf |= fu;
-            }
+            if (lane - off >= seg) v += vu;
         }
         float cin = __shfl_up_sync(0xffffffffu, v, 1);
         if (lane == 0) cin = 0.f;

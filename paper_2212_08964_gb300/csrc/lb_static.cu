@@ -72,6 +72,7 @@ lb_status status_of(cudaError_t e) { return e == cudaSuccess ? LB_OK : LB_ERR_CU
 extern "C" lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offsets, const int *col_idx,
                                     const void *values, lb_dtype vdt, const float *x, float *y,
                                     cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (m < 0 || n < 0 || nnz < 0 || ((m == 0 || n == 0) && nnz != 0)) return LB_ERR_INVALID_ARG;
     if (vdt != LB_F32 && vdt != LB_BF16 && vdt != LB_F16) return LB_ERR_INVALID_ARG;
     if (m == 0) return LB_OK;
@@ -110,6 +111,7 @@ extern "C" lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offset
     a.idx = col_idx;
     a.val = values;
     a.x = x;
+    a.x_len = n;
     a.y = y;
     a.carry_row = carry_row;
     a.carry_val = carry_val;

@@ -255,7 +255,7 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
     const size_t ints = static_cast<size_t>(nnz) * 3 + static_cast<size_t>(hist_n) +
                         static_cast<size_t>(scan_scratch_ints(scan_n));
     int *work = nullptr;
-    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&work), ints * sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = dev_malloc_async(reinterpret_cast<void **>(&work), ints * sizeof(int), st)) != cudaSuccess) return e;
     int *rowid = work;
     int *keys_a = rowid + nnz;
     int *vals_a = keys_a + nnz;
@@ -295,7 +295,7 @@ cudaError_t build_transpose(int m, int n, int nnz, const int *ro, const int *ci,
         e = cudaGetLastError();
     }
 done:
-    cudaError_t e2 = cudaFreeAsync(work, st);
+    cudaError_t e2 = dev_free_async(work, st);
     return e != cudaSuccess ? e : e2;
 }
 
@@ -338,7 +338,7 @@ cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket
     const size_t ints = 2 * static_cast<size_t>(nnz) + static_cast<size_t>(hist_n) +
                         static_cast<size_t>(scan_scratch_ints(hist_n));
     int *work = nullptr;
-    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&work), ints * sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = dev_malloc_async(reinterpret_cast<void **>(&work), ints * sizeof(int), st)) != cudaSuccess) return e;
     int *pinv = work;            // CSR entry -> CSC position
     int *order = pinv + nnz;     // bucket order -> CSR entry
     int *hist = order + nnz;
@@ -354,7 +354,7 @@ cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket
         gather_kernel<<<grid, 256, 0, st>>>(bucket_pos, perm, bucket_perm, nnz);  // bucket_perm[p] = bucket_pos[perm[p]]
         e = cudaGetLastError();
     }
-    cudaError_t e2 = cudaFreeAsync(work, st);
+    cudaError_t e2 = dev_free_async(work, st);
     return e != cudaSuccess ? e : e2;
 }
 

@@ -59,6 +59,7 @@ extern "C" int lb_tune_candidates(void) { return static_cast<int>(all_candidates
 extern "C" lb_status lb_tune(int m, int n, int nnz, const int *row_offsets, const int *col_idx, const void *values,
                              lb_dtype vdt, const float *x, float *y, int reps, lb_tune_result *results, int capacity,
                              int *count, cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!count || !results || capacity < 0 || reps <= 0) return LB_ERR_INVALID_ARG;
     *count = 0;
     if (m <= 0 || n <= 0 || nnz <= 0 || !row_offsets || !col_idx || !values || !x || !y) return LB_ERR_INVALID_ARG;
@@ -92,6 +93,7 @@ extern "C" lb_status lb_tune_batched(int count_m, const int *h_m, const int *h_n
                                      const void *values_concat, lb_dtype vdt, const float *x_concat,
                                      float *y_concat, int reps, lb_tune_result *results, int capacity, int *count,
                                      cudaStream_t stream) {
+    LB_NVTX_RANGE();
     if (!count || !results || capacity < 0 || reps <= 0) return LB_ERR_INVALID_ARG;
     *count = 0;
     if (count_m <= 0 || !h_m || !h_n || !h_nnz || !row_offsets_concat || !col_idx_concat || !values_concat ||

@@ -49,11 +49,9 @@ __device__ __forceinline__ void st_stream8(void *p, uint64_t pol, const float *v
 // Lane mask of this lane's slots that hold the tile's nonzeros: slot q holds element e0 + q.
 template <int IPT>
 __device__ __forceinline__ uint32_t slot_mask(int e0, int k0, int k1) {
-    uint32_t m = 0;
-#pragma unroll
-    for (int q = 0; q < IPT; ++q)
-        if (e0 + q >= k0 && e0 + q < k1) m |= 1u << q;
-    return m;
+    const int lo = min(max(k0 - e0, 0), IPT);  // slots [lo, hi) lie in [k0, k1)
+    const int hi = min(max(k1 - e0, 0), IPT);
+    return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
 }
 
 // A 16-bit value's bits widened to FP32 (BF16: shift into the high half; FP16: convert).

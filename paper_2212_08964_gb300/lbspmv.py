@@ -148,6 +148,10 @@ def _declare(lib):
     lib.lb_plan_destroy.restype = None
     lib.lb_batched_plan_destroy.argtypes = [_P]
     lib.lb_batched_plan_destroy.restype = None
+    lib.lb_debug_fail_allocations_after.argtypes = [_I]
+    lib.lb_debug_fail_allocations_after.restype = None
+    lib.lb_debug_live_allocations.argtypes = []
+    lib.lb_debug_live_allocations.restype = ctypes.c_longlong
 
 
 def library_path() -> str:
@@ -651,3 +655,14 @@ def set_profile_events(before: torch.cuda.Event | None, after: torch.cuda.Event 
     b = before.cuda_event if before is not None else None
     a = after.cuda_event if after is not None else None
     _check(lib.lb_set_profile_events(b, a), "lb_set_profile_events")
+
+
+def fail_allocations_after(count: int):
+    """Test support: the library's next `count` device allocations proceed, later ones fail
+    as if the device were full (LB_ERR_NO_MEMORY); a negative count removes the limit."""
+    ensure_loaded().lb_debug_fail_allocations_after(int(count))
+
+
+def live_allocations() -> int:
+    """The library's device allocations currently held."""
+    return int(ensure_loaded().lb_debug_live_allocations())

@@ -79,3 +79,18 @@ def test_host_side_argument_rejection(lib):
     assert lib.lb_spmv_batched(None, None, None, 0, None, None, None) == -1
     assert lib.lb_validate_csr(-1, 0, 0, None, None, 0, None, None) == -1
     assert lib.lb_device_error(None, 0) == -1
+
+
+def test_allocation_failure_injection_on_host(lib):
+    """A plan whose first device allocation fails reports LB_ERR_NO_MEMORY, returns no plan
+    and holds nothing; the failure is injected on the host, before any device memory."""
+    lib.lb_debug_live_allocations.restype = ctypes.c_longlong
+    out = ctypes.c_void_p()
+    live = lib.lb_debug_live_allocations()
+    lib.lb_debug_fail_allocations_after(0)
+    try:
+        assert lib.lb_plan_create(4, 4, 4, ctypes.c_void_p(16), 5, None, None, ctypes.byref(out)) == -4
+        assert out.value is None
+        assert lib.lb_debug_live_allocations() == live
+    finally:
+        lib.lb_debug_fail_allocations_after(-1)
