@@ -534,7 +534,7 @@ lb_status lb_spmv_planned(const lb_plan *p, const int *col_idx, const void *valu
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return from_cuda(cudaMemsetAsync(y, 0, static_cast<size_t>(p->m) * sizeof(float), stream));
     if (p->sched == LB_SCHED_NONZERO_SPLIT)
-        return from_cuda(launch_nzsplit(vdt, p->G_nz, p->m, p->nnz, p->nz_first, p->nz_last, p->ro, col_idx, values, x,
+        return from_cuda(launch_nzsplit(vdt, p->G_nz, p->m, p->n, p->nnz, p->nz_first, p->nz_last, p->ro, col_idx, values, x,
                                         y, p->nz_carry_row, p->nz_carry_val, stream));
     if (p->sched != LB_SCHED_MERGE_PATH)
         return from_cuda(launch_mapped(p->sched, p->tune, vdt, p->m, p->n, p->nnz, p->ro, col_idx, values, x, y, stream));
@@ -741,7 +741,7 @@ lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb
         if (e != cudaSuccess) return from_cuda(e);
         p->mm_cols = kc;
     }
-    return from_cuda(launch_spmm(vdt, p->G, p->m, kc, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx,
+    return from_cuda(launch_spmm(vdt, p->G, p->m, p->n, kc, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx,
                                  values, B, C, p->mm_carry_row, p->mm_carry_val, stream));
 }
 

@@ -42,7 +42,7 @@ __global__ void frontier_degrees_kernel(int fsize, const int *__restrict__ front
 }
 
 // Relax edges [0, total) of the frontier; pre[i] = first edge of frontier vertex i.
-__global__ void __launch_bounds__(kGraphThreads) relax_kernel(int fsize, int iter, const int *__restrict__ frontier,
+__global__ void __launch_bounds__(kGraphThreads) relax_kernel(int n, int fsize, int iter, const int *__restrict__ frontier,
                                                               const int *__restrict__ pre, const int *__restrict__ ro,
                                                               const int *__restrict__ ci, const float *__restrict__ w,
                                                               float *dist, int *stamp, int *next, int *next_count) {
@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kGraphThreads) relax_kernel(int fsize, int ite
         const int u = __ldg(frontier + lo);
         const long long k = __ldg(ro + u) + (e - __ldg(pre + lo));
         const int v = __ldg(ci + k);
+        if (!LB_IN_RANGE(v, n)) continue;
         const float nd = dist[u] + (w ? __ldg(w + k) : 1.f);
         const int old = atomicMin(reinterpret_cast<int *>(dist) + v, __float_as_int(nd));
         if (nd < __int_as_float(old) && atomicMax(stamp + v, iter) < iter) next[atomicAdd(next_count, 1)] = v;
@@ -105,7 +106,7 @@ cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *
         if ((e = exclusive_scan(pre, pre, static_cast<long long>(fsize) + 1, sums, st)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(d_count, 0, sizeof(int), st)) != cudaSuccess) break;
         // The edge count stays on the device; the relaxation reads it and strides over it.
-        relax_kernel<<<sms * 16, kGraphThreads, 0, st>>>(fsize, iter, f_cur, pre, ro, ci, w, dist, stamp, f_next,
+        relax_kernel<<<sms * 16, kGraphThreads, 0, st>>>(n, fsize, iter, f_cur, pre, ro, ci, w, dist, stamp, f_next,
                                                          d_count);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;

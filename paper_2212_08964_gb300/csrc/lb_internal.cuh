@@ -183,7 +183,7 @@ cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, con
 
 // SpMM C = A B (B dense n x kc row-major, C m x kc) over the forward partition (tiles of at
 // most 2048 items), then the fixup of the carries (carry_row[G], carry_val[G * kc]).
-cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, const int *tile_row, const int *tile_nz,
+cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int n, int kc, int tile_items, const int *tile_row, const int *tile_nz,
                         const int *row_end, const int *ci, const void *values, const float *B, float *C,
                         int *carry_row, float *carry_val, cudaStream_t st);
 
@@ -193,7 +193,7 @@ cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, cons
 int nzsplit_tile_nonzeros();
 cudaError_t launch_nz_partition(int G, int m, int nnz, const int *ro, int *first_row, int *last_row,
                                 cudaStream_t st);
-cudaError_t launch_nzsplit(lb_dtype vdt, int G, int m, int nnz, const int *first_row, const int *last_row,
+cudaError_t launch_nzsplit(lb_dtype vdt, int G, int m, int n, int nnz, const int *first_row, const int *last_row,
                            const int *ro, const int *ci, const void *values, const float *x, float *y,
                            int *carry_row, float *carry_val, cudaStream_t st);
 

@@ -72,7 +72,7 @@ __device__ __forceinline__ void load8_values(const H *p, float (&o)[8]) {
 }
 
 template <typename V>
-__global__ void __launch_bounds__(kNzThreads) nzsplit_kernel(int G, int m, int nnz, const int *__restrict__ first_row,
+__global__ void __launch_bounds__(kNzThreads) nzsplit_kernel(int G, int m, int n, int nnz, const int *__restrict__ first_row,
                                                              const int *__restrict__ last_row,
                                                              const int *__restrict__ ro, const int *__restrict__ ci,
                                                              const V *__restrict__ values, const float *__restrict__ x,
@@ -109,12 +109,16 @@ __global__ void __launch_bounds__(kNzThreads) nzsplit_kernel(int G, int m, int n
             col[4] = c1.x; col[5] = c1.y; col[6] = c1.z; col[7] = c1.w;
             load8_values(values + k0 + j0, val);
 #pragma unroll
-            for (int q = 0; q < kNzIpt; ++q) prod[q] = val[q] * __ldg(x + col[q]);
+            for (int q = 0; q < kNzIpt; ++q) prod[q] = LB_IN_RANGE(col[q], n) ? val[q] * __ldg(x + col[q]) : 0.f;
         } else {
 #pragma unroll
             for (int q = 0; q < kNzIpt; ++q) {
                 const int j = j0 + q;
-                prod[q] = j < nk ? to_f32(values[k0 + j]) * __ldg(x + __ldg(ci + k0 + j)) : 0.f;
+                prod[q] = 0.f;
+                if (j < nk) {
+                    const int c = __ldg(ci + k0 + j);
+                    if (LB_IN_RANGE(c, n)) prod[q] = to_f32(values[k0 + j]) * __ldg(x + c);
+                }
             }
         }
         // Rows starting inside the tile (empty rows included: they share a start).
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kNzThreads) nzsplit_kernel(int G, int m, int n
 }
 
 template <typename V>
-cudaError_t launch_nzsplit_t(int G, int m, int nnz, const int *first_row, const int *last_row, const int *ro,
+cudaError_t launch_nzsplit_t(int G, int m, int n, int nnz, const int *first_row, const int *last_row, const int *ro,
                              const int *ci, const void *values, const float *x, float *y, int *carry_row,
                              float *carry_val, cudaStream_t st) {
     auto kern = nzsplit_kernel<V>;
@@ -235,7 +239,7 @@ cudaError_t launch_nzsplit_t(int G, int m, int nnz, const int *first_row, const 
     if (e != cudaSuccess) return e;
     long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
     if (grid > G) grid = G;
-    kern<<<static_cast<int>(grid), kNzThreads, 0, st>>>(G, m, nnz, first_row, last_row, ro, ci,
+    kern<<<static_cast<int>(grid), kNzThreads, 0, st>>>(G, m, n, nnz, first_row, last_row, ro, ci,
                                                          static_cast<const V *>(values), x, y, carry_row, carry_val);
     return cudaGetLastError();
 }
@@ -254,21 +258,21 @@ cudaError_t launch_nz_partition(int G, int m, int nnz, const int *ro, int *first
     return cudaGetLastError();
 }
 
-cudaError_t launch_nzsplit(lb_dtype vdt, int G, int m, int nnz, const int *first_row, const int *last_row,
+cudaError_t launch_nzsplit(lb_dtype vdt, int G, int m, int n, int nnz, const int *first_row, const int *last_row,
                            const int *ro, const int *ci, const void *values, const float *x, float *y,
                            int *carry_row, float *carry_val, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(y, 0, static_cast<size_t>(m) * sizeof(float), st);
     if (e != cudaSuccess || G <= 0) return e;
     switch (vdt) {
         case LB_F32:
-            e = launch_nzsplit_t<float>(G, m, nnz, first_row, last_row, ro, ci, values, x, y, carry_row, carry_val, st);
+            e = launch_nzsplit_t<float>(G, m, n, nnz, first_row, last_row, ro, ci, values, x, y, carry_row, carry_val, st);
             break;
         case LB_BF16:
-            e = launch_nzsplit_t<__nv_bfloat16>(G, m, nnz, first_row, last_row, ro, ci, values, x, y, carry_row,
+            e = launch_nzsplit_t<__nv_bfloat16>(G, m, n, nnz, first_row, last_row, ro, ci, values, x, y, carry_row,
                                                 carry_val, st);
             break;
         case LB_F16:
-            e = launch_nzsplit_t<__half>(G, m, nnz, first_row, last_row, ro, ci, values, x, y, carry_row, carry_val,
+            e = launch_nzsplit_t<__half>(G, m, n, nnz, first_row, last_row, ro, ci, values, x, y, carry_row, carry_val,
                                          st);
             break;
         default:

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(256) partition_kernel(int m, long long W, int 
                 const long long c = c_own + (q - e_own);
                 const long long row = base + lo;
                 const long long d = c * T < W ? c * T : W;
+                if (!LB_IN_RANGE(c, G + 1)) continue;
                 tile_row[c] = static_cast<int>(row);
                 tile_nz[c] = static_cast<int>(d - row);
             }

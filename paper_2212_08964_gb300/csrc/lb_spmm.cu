@@ -67,7 +67,7 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(
 
 // NQ column quads per pass (a power of two, <= THREADS); NG = THREADS / NQ nonzero ranges.
 template <typename V, int THREADS, int TMAX, bool VEC>
-__global__ void __launch_bounds__(THREADS) spmm_kernel(int G, int m, int kc, int nq, const int *__restrict__ tile_row,
+__global__ void __launch_bounds__(THREADS) spmm_kernel(int G, int m, int n, int kc, int nq, const int *__restrict__ tile_row,
                                                        const int *__restrict__ tile_nz,
                                                        const int *__restrict__ row_end, const int *__restrict__ ci,
                                                        const V *__restrict__ values, const float *__restrict__ B,
@@ -95,8 +95,10 @@ __global__ void __launch_bounds__(THREADS) spmm_kernel(int G, int m, int kc, int
         const int nr = r1 - r0, nk = k1 - k0;
         if (nr < 0 || nk < 0 || nr > TMAX || nk > TMAX) continue;  // malformed offsets (block-uniform)
         for (int j = tid; j < nk; j += THREADS) {
-            s_col[j] = __ldg(ci + k0 + j);
-            s_val[j] = to_f32(values[k0 + j]);
+            const int c = __ldg(ci + k0 + j);
+            const bool in = LB_IN_RANGE(c, n);  // always true outside the range-checked build
+            s_col[j] = in ? c : 0;
+            s_val[j] = in ? to_f32(values[k0 + j]) : 0.f;
         }
         for (int r = tid; r < nr; r += THREADS) {
             const int e = __ldg(row_end + r0 + r) - k0;  // first nonzero of the next row, tile-local
@@ -304,7 +306,7 @@ __global__ void spmm_fixup_kernel(int G, int m, int kc, const int *__restrict__ 
 }
 
 template <typename V, int TMAX, bool VEC>
-static cudaError_t launch_spmm_t(int G, int m, int kc, const int *tile_row, const int *tile_nz, const int *row_end,
+static cudaError_t launch_spmm_t(int G, int m, int n, int kc, const int *tile_row, const int *tile_nz, const int *row_end,
                                  const int *ci, const V *values, const float *B, float *C, int *carry_row,
                                  float *carry_val, cudaStream_t st) {
     constexpr int THREADS = 256;
@@ -317,7 +319,7 @@ static cudaError_t launch_spmm_t(int G, int m, int kc, const int *tile_row, cons
     if (e != cudaSuccess) return e;
     long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
     if (grid > G) grid = G;
-    kern<<<static_cast<int>(grid), THREADS, 0, st>>>(G, m, kc, nq, tile_row, tile_nz, row_end, ci, values, B, C,
+    kern<<<static_cast<int>(grid), THREADS, 0, st>>>(G, m, n, kc, nq, tile_row, tile_nz, row_end, ci, values, B, C,
                                                      carry_row, carry_val);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     long long fb = (static_cast<long long>(G) + 7) / 8;
@@ -328,32 +330,32 @@ static cudaError_t launch_spmm_t(int G, int m, int kc, const int *tile_row, cons
 }
 
 template <typename V>
-static cudaError_t launch_spmm_v(int G, int m, int kc, int tile_items, const int *tile_row, const int *tile_nz,
+static cudaError_t launch_spmm_v(int G, int m, int n, int kc, int tile_items, const int *tile_row, const int *tile_nz,
                                  const int *row_end, const int *ci, const void *values, const float *B, float *C,
                                  int *carry_row, float *carry_val, cudaStream_t st) {
     const V *v = static_cast<const V *>(values);
     const bool vec = kc % 4 == 0 && (reinterpret_cast<uintptr_t>(B) & 15u) == 0 &&
                      (reinterpret_cast<uintptr_t>(C) & 15u) == 0;
     if (tile_items > 2048) return cudaErrorInvalidValue;  // shared-memory staging holds 2048 items
-    return vec ? launch_spmm_t<V, 2048, true>(G, m, kc, tile_row, tile_nz, row_end, ci, v, B, C, carry_row, carry_val,
+    return vec ? launch_spmm_t<V, 2048, true>(G, m, n, kc, tile_row, tile_nz, row_end, ci, v, B, C, carry_row, carry_val,
                                               st)
-               : launch_spmm_t<V, 2048, false>(G, m, kc, tile_row, tile_nz, row_end, ci, v, B, C, carry_row,
+               : launch_spmm_t<V, 2048, false>(G, m, n, kc, tile_row, tile_nz, row_end, ci, v, B, C, carry_row,
                                                carry_val, st);
 }
 
-cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int kc, int tile_items, const int *tile_row, const int *tile_nz,
+cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int n, int kc, int tile_items, const int *tile_row, const int *tile_nz,
                         const int *row_end, const int *ci, const void *values, const float *B, float *C,
                         int *carry_row, float *carry_val, cudaStream_t st) {
     if (G <= 0) return cudaSuccess;
     switch (vdt) {
         case LB_F32:
-            return launch_spmm_v<float>(G, m, kc, tile_items, tile_row, tile_nz, row_end, ci, values, B, C, carry_row,
+            return launch_spmm_v<float>(G, m, n, kc, tile_items, tile_row, tile_nz, row_end, ci, values, B, C, carry_row,
                                         carry_val, st);
         case LB_BF16:
-            return launch_spmm_v<__nv_bfloat16>(G, m, kc, tile_items, tile_row, tile_nz, row_end, ci, values, B, C,
+            return launch_spmm_v<__nv_bfloat16>(G, m, n, kc, tile_items, tile_row, tile_nz, row_end, ci, values, B, C,
                                                 carry_row, carry_val, st);
         case LB_F16:
-            return launch_spmm_v<__half>(G, m, kc, tile_items, tile_row, tile_nz, row_end, ci, values, B, C, carry_row,
+            return launch_spmm_v<__half>(G, m, n, kc, tile_items, tile_row, tile_nz, row_end, ci, values, B, C, carry_row,
                                          carry_val, st);
     }
     return cudaErrorInvalidValue;
