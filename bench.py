@@ -837,55 +837,76 @@ def run_sssp(lb, torch, dev, a, ro, ci):
     return out
 
 
-def run_batched(lb, torch, dev):
-    """4096 matrices of uneven size: one persistent launch replayed from a CUDA graph against one
-    planned call per matrix (the plain per-matrix form)."""
-    from paper_2212_08964_gb300 import synth
-
-    out = {}
-    b = synth.workload("batched_4096")
-    xs = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(5), int(b.ns.sum()))).to(dev)
-    bci, bv = torch.from_numpy(b.col_idx).to(dev), torch.from_numpy(b.values).to(dev)
-    bro = torch.from_numpy(b.row_offsets).to(dev)
-    bp = lb.BatchedPlan(b.ms, b.ns, b.nnzs, bro)
-    yb = torch.empty(int(b.ms.sum()), device=dev)
+def _graph_ms(torch, fn, reps=20):
+    """Mean ms of one call of fn replayed from a CUDA graph (fn's first call runs outside
+    the capture: kernel attributes are set there)."""
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        bp.spmv(bci, bv, xs, out=yb)  # first call outside the capture (kernel attributes)
+        fn()
     torch.cuda.current_stream().wait_stream(s)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        bp.spmv(bci, bv, xs, out=yb)
-    ms_b = _time(torch, graph.replay, 20)
-    total = sum(spmv_bytes(int(m), int(n), int(z)) for m, n, z in zip(b.ms, b.ns, b.nnzs))
-    info = bp.info()
-    out["workload"] = f"batched_4096: {b.count} matrices, {int(b.ms.sum())} rows, {int(b.nnzs.sum())} nonzeros"
-    out["graph_ms"] = ms_b
-    out["graph_GBps"] = total / (ms_b * 1e-3) / 1e9
-    out["graph_launches"] = 2
-    out["shape"] = [info["threads"], info["items_per_thread"]]
-    plans, views = [], []
-    ro_pos = nz_pos = x_pos = y_pos = 0
-    for i in range(b.count):
-        m, n, z = int(b.ms[i]), int(b.ns[i]), int(b.nnzs[i])
-        p = lb.Plan(bro[ro_pos: ro_pos + m + 1], n, z, schedule="auto")
-        plans.append(p)
-        views.append((bci[nz_pos: nz_pos + z], bv[nz_pos: nz_pos + z], xs[x_pos: x_pos + n], yb[y_pos: y_pos + m]))
-        ro_pos += m + 1
-        nz_pos += z
-        x_pos += n
-        y_pos += m
+        fn()
+    return _time(torch, graph.replay, reps)
 
-    def per_matrix():
-        for p, (c_, v_, x_, y_) in zip(plans, views):
-            p.spmv(c_, v_, x_, out=y_)
 
-    ms_p = _time(torch, per_matrix, 3)
-    out["per_matrix_ms"] = ms_p
-    out["per_matrix_GBps"] = total / (ms_p * 1e-3) / 1e9
-    out["per_matrix_launches"] = 2 * b.count
-    out["speedup_vs_per_matrix"] = ms_p / ms_b
+def run_batched(lb, torch, dev):
+    """Two batch classes, each as one launch replayed from a CUDA graph under both batch
+    schedules (the global merge path; thread-mapped rows with long rows summed by the warp)
+    and in the shipped table's choice for its class; batched_4096 also against one planned
+    call per matrix (the plain per-matrix form)."""
+    from paper_2212_08964_gb300 import autotune, synth
+
+    table = autotune.default_table()
+    out = {}
+    for name in ("batched_4096", "batched_grid_1024"):
+        b = synth.workload(name)
+        xs = torch.from_numpy(synth.uniform_pm1(np.random.default_rng(5), int(b.ns.sum()))).to(dev)
+        bci, bv = torch.from_numpy(b.col_idx).to(dev), torch.from_numpy(b.values).to(dev)
+        bro = torch.from_numpy(b.row_offsets).to(dev)
+        yb = torch.empty(int(b.ms.sum()), device=dev)
+        total = sum(spmv_bytes(int(m), int(n), int(z)) for m, n, z in zip(b.ms, b.ns, b.nnzs))
+        r = {"workload": f"{name}: {b.count} matrices, {int(b.ms.sum())} rows, {int(b.nnzs.sum())} nonzeros",
+             "bytes": total}
+        for sched in ("merge_path", "thread_mapped"):
+            bp = lb.BatchedPlan(b.ms, b.ns, b.nnzs, bro, schedule=sched)
+            ms_b = _graph_ms(torch, lambda: bp.spmv(bci, bv, xs, out=yb))
+            r[sched] = {"graph_ms": ms_b, "graph_GBps": total / (ms_b * 1e-3) / 1e9,
+                        "launches": 2 if sched == "merge_path" else 1}
+            bp.close()
+        bp = autotune.batched_plan_for(b.ms, b.ns, b.nnzs, bro, table)
+        info = bp.info()
+        ms_t = _graph_ms(torch, lambda: bp.spmv(bci, bv, xs, out=yb))
+        r["tuned"] = {"schedule": info["schedule"], "shape": [info["threads"], info["items_per_thread"]],
+                      "graph_ms": ms_t, "graph_GBps": total / (ms_t * 1e-3) / 1e9}
+        if name == "batched_4096":
+            plans, views = [], []
+            ro_pos = nz_pos = x_pos = y_pos = 0
+            for i in range(b.count):
+                m, n, z = int(b.ms[i]), int(b.ns[i]), int(b.nnzs[i])
+                p = lb.Plan(bro[ro_pos: ro_pos + m + 1], n, z, schedule="auto")
+                plans.append(p)
+                views.append((bci[nz_pos: nz_pos + z], bv[nz_pos: nz_pos + z], xs[x_pos: x_pos + n],
+                              yb[y_pos: y_pos + m]))
+                ro_pos += m + 1
+                nz_pos += z
+                x_pos += n
+                y_pos += m
+
+            def per_matrix():
+                for p, (c_, v_, x_, y_) in zip(plans, views):
+                    p.spmv(c_, v_, x_, out=y_)
+
+            ms_p = _time(torch, per_matrix, 3)
+            r["per_matrix_ms"] = ms_p
+            r["per_matrix_GBps"] = total / (ms_p * 1e-3) / 1e9
+            r["per_matrix_launches"] = 2 * b.count
+            r["tuned_speedup_vs_per_matrix"] = ms_p / ms_t
+            for p in plans:
+                p.close()
+        out[name] = r
+        del b, bci, bv, bro, yb, xs
     return out
 
 

@@ -301,8 +301,15 @@ void lb_plan_destroy(lb_plan *p);
  * structure one level up).  h_m, h_n, h_nnz: HOST arrays of `count` sizes.
  * row_offsets_concat (device) concatenates each matrix's own offsets (m_i + 1 entries,
  * each starting at 0).  The plan materializes the block-diagonal row offsets and one
- * global merge-path partition over sum(m_i + nnz_i).  s must be LB_SCHED_AUTO or
- * LB_SCHED_MERGE_PATH.
+ * global merge-path partition over sum(m_i + nnz_i).  Schedules:
+ *   LB_SCHED_MERGE_PATH (and LB_SCHED_AUTO): the global merge path, one persistent launch
+ *     plus the fixup; t picks its launch shape.
+ *   LB_SCHED_THREAD_MAPPED: a row per lane over the block-diagonal matrix (Ch.3 Sec.
+ *     "Thread-Mapped"), rows longer than 32 nonzeros summed by the lane's whole warp (the
+ *     group-mapped remedy, Ch.3 Sec. "Group-Mapped"); one launch, no carries.  Suited to
+ *     batches of mostly very short rows; t must be NULL or zero.
+ * Other schedules return LB_ERR_UNSUPPORTED.  The autotuner (lb_tune_batched) measures both
+ * for a batch's shape class.
  */
 lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, const int *h_nnz,
                                  const int *row_offsets_concat, lb_schedule s, const lb_tuning *t,
@@ -312,12 +319,16 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
  * be NULL). */
 lb_status lb_batched_plan_info(const lb_batched_plan *p, lb_tuning *t, int *num_tiles, int *tile_items);
 
+/* The schedule a batched plan runs (LB_SCHED_MERGE_PATH or LB_SCHED_THREAD_MAPPED). */
+lb_status lb_batched_plan_schedule(const lb_batched_plan *p, lb_schedule *s);
+
 /* Copy the global partition to HOST arrays of num_tiles + 1 ints (synchronizes). */
 lb_status lb_batched_plan_partition(const lb_batched_plan *p, int *tile_row, int *tile_nz,
                                     int *num_tiles);
 
 /*
- * y_i = A_i x_i for every matrix of the plan in ONE persistent launch plus the fixup.
+ * y_i = A_i x_i for every matrix of the plan in ONE persistent launch plus the fixup (one
+ * launch and no fixup under the thread-mapped schedule).
  * col_idx_concat holds local column indices; values_concat, x_concat (sum n_i floats) and
  * y_concat (sum m_i floats) are concatenated in matrix order.  No allocation.
  */
@@ -351,8 +362,9 @@ lb_status lb_tune(int m, int n, int nnz, const int *row_offsets, const int *col_
                   int *count, cudaStream_t stream);
 
 /*
- * The same for a batch run as one block-diagonal merge path (arguments as for
- * lb_batched_plan_create and lb_spmv_batched): every merge-path launch shape, timed.
+ * The same for a batch (arguments as for lb_batched_plan_create and lb_spmv_batched): the
+ * thread-mapped batch schedule and the block-diagonal merge path at every launch shape,
+ * timed.
  */
 lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *h_nnz,
                           const int *row_offsets_concat, const int *col_idx_concat, const void *values_concat,

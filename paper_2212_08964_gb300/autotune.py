@@ -38,7 +38,7 @@ import numpy as np
 
 from . import lbspmv
 
-__all__ = ["shape_class", "lrb_bins", "batch_class", "Table", "tune", "tune_batched", "choose", "plan_for", "predict",
+__all__ = ["shape_class", "lrb_bins", "batch_class", "Table", "tune", "tune_batched", "choose", "plan_for", "batched_plan_for", "predict",
            "choose_by_roofline", "build_table", "default_table", "DEFAULT_TABLE", "STANDARD_WORKLOADS"]
 
 _SKEW_EDGES = (1.5, 4.0, 32.0, 256.0)
@@ -197,7 +197,8 @@ def tune(row_offsets, col_idx, values, x, n: int | None = None, reps: int = 20, 
 
 def tune_batched(ms, ns, nnzs, row_offsets_concat, col_idx_concat, values_concat, x_concat, reps: int = 10,
                  table: Table | None = None, stream=None) -> list[dict]:
-    """Time every merge-path launch shape on this batch; with ``table``, record the winner."""
+    """Time the batch schedules on this batch (thread-mapped rows, and the global merge path at
+    every launch shape); with ``table``, record the winner for the batch's class."""
     import torch
 
     lib = lbspmv.ensure_loaded()
@@ -230,7 +231,7 @@ def default_table() -> Table | None:
     return Table.load(DEFAULT_TABLE) if os.path.exists(DEFAULT_TABLE) else None
 
 
-def build_table(workloads=STANDARD_WORKLOADS, dtypes=("f32", "bf16", "f16"), batched=("batched_4096",), reps: int = 10,
+def build_table(workloads=STANDARD_WORKLOADS, dtypes=("f32", "bf16", "f16"), batched=("batched_4096", "batched_grid_1024"), reps: int = 10,
                 table: Table | None = None, log=None) -> Table:
     """Tune every workload in every value type (and every batch) on the current GPU and
     record the winners by shape class."""
@@ -258,7 +259,8 @@ def build_table(workloads=STANDARD_WORKLOADS, dtypes=("f32", "bf16", "f16"), bat
                            torch.from_numpy(b.col_idx).cuda(), torch.from_numpy(b.values).cuda(), xs, reps=reps,
                            table=table)
         if log:
-            log(f"{name}: ({res[0]['threads']}, {res[0]['items_per_thread']}) {res[0]['ms'] * 1e3:.1f} us")
+            log(f"{name}: {res[0]['schedule']} ({res[0]['threads']}, {res[0]['items_per_thread']}) "
+                f"{res[0]['ms'] * 1e3:.1f} us")
     return table
 
 
@@ -274,6 +276,17 @@ def plan_for(row_offsets, n: int, table: Table | None, dtype: str = "f32", strea
     cfg = choose(row_offsets.cpu().numpy(), table, dtype)
     return lbspmv.Plan(row_offsets, n, schedule=cfg["schedule"], threads=cfg["threads"],
                        items_per_thread=cfg["items_per_thread"], group_size=cfg["group_size"], stream=stream)
+
+
+def batched_plan_for(ms, ns, nnzs, row_offsets_concat, table: Table | None, dtype: str = "f32",
+                     stream=None) -> "lbspmv.BatchedPlan":
+    """A BatchedPlan with the table's schedule and shape for the batch's class (the global
+    merge path at the default shape when the class is not in the table)."""
+    best = table.lookup(batch_class(ms, nnzs, row_offsets_concat.cpu().numpy(), dtype)) if table is not None else None
+    if best is None or best["schedule"] not in ("merge_path", "thread_mapped"):
+        best = {"schedule": "merge_path", "threads": 0, "items_per_thread": 0}
+    return lbspmv.BatchedPlan(ms, ns, nnzs, row_offsets_concat, threads=best["threads"],
+                              items_per_thread=best["items_per_thread"], schedule=best["schedule"], stream=stream)
 
 
 if __name__ == "__main__":

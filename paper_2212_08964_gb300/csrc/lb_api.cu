@@ -228,10 +228,11 @@ struct lb_batched_plan {
     int device = -1;
     int count = 0, kc = 0;
     long long total_rows = 0, total_cols = 0, total_nnz = 0;
+    lb_schedule sched = LB_SCHED_MERGE_PATH;
     lb_tuning tune = {0, 0, 0};
     int tile_items = 0;
     int G = 0;
-    int *ro_g = nullptr, *mat_nz_base = nullptr, *mat_col_base = nullptr;
+    int *ro_g = nullptr, *mat_nz_base = nullptr, *mat_col_base = nullptr, *mat_row_base = nullptr;
     int *tile_row = nullptr, *tile_nz = nullptr, *tile_mat = nullptr, *carry_row = nullptr;
     float *carry_val = nullptr;
 };
@@ -758,8 +759,13 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     if (!out) return LB_ERR_INVALID_ARG;
     *out = nullptr;
     if (count < 0 || (count > 0 && (!h_m || !h_n || !h_nnz))) return LB_ERR_INVALID_ARG;
-    if (s != LB_SCHED_AUTO && s != LB_SCHED_MERGE_PATH) return LB_ERR_UNSUPPORTED;
+    if (!sched_ok(s)) return LB_ERR_INVALID_ARG;
+    if (s != LB_SCHED_AUTO && s != LB_SCHED_MERGE_PATH && s != LB_SCHED_THREAD_MAPPED) return LB_ERR_UNSUPPORTED;
     lb_tuning r = t ? *t : lb_tuning{0, 0, 0};
+    if (s == LB_SCHED_THREAD_MAPPED) {
+        if (r.threads != 0 && r.threads != kDefaultThreads) return LB_ERR_INVALID_ARG;
+        r = lb_tuning{0, 0, 0};  // the partition below still uses the default merge tiles
+    }
     if (r.threads == 0) r.threads = kDefaultThreads;
     if (r.items_per_thread == 0) r.items_per_thread = kDefaultIpt;
     if (!merge_shape_ok(r.threads, r.items_per_thread)) return LB_ERR_INVALID_ARG;
@@ -790,15 +796,15 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     p->total_rows = rows;
     p->total_cols = cols;
     p->total_nnz = nnz;
+    p->sched = s == LB_SCHED_THREAD_MAPPED ? LB_SCHED_THREAD_MAPPED : LB_SCHED_MERGE_PATH;
     p->tune = r;
     p->tile_items = merge_tile_items(r.items_per_thread);
     p->G = num_tiles_of(rows, nnz, p->tile_items);
     const int kc = p->kc;
-    int *d_ro_pos = nullptr, *d_row_base = nullptr;
+    int *d_ro_pos = nullptr;
     cudaError_t e = cudaSuccess;
     auto fail = [&](cudaError_t err) {
         if (d_ro_pos) dev_free(d_ro_pos);
-        if (d_row_base) dev_free(d_row_base);
         lb_batched_plan_destroy(p);
         return from_cuda(err);
     };
@@ -811,7 +817,7 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
         (e = dmalloc(&p->carry_row, static_cast<size_t>(p->G))) != cudaSuccess ||
         (e = dmalloc(&p->carry_val, static_cast<size_t>(p->G))) != cudaSuccess ||
         (e = dmalloc(&d_ro_pos, static_cast<size_t>(kc) + 1)) != cudaSuccess ||
-        (e = dmalloc(&d_row_base, static_cast<size_t>(kc) + 1)) != cudaSuccess)
+        (e = dmalloc(&p->mat_row_base, static_cast<size_t>(kc) + 1)) != cudaSuccess)
         return fail(e);
     if (kc == 0) {
         const int zero = 0;
@@ -821,18 +827,18 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
         if (e == cudaSuccess) e = cudaMemcpy(p->tile_mat, &zero, sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(e);
         dev_free(d_ro_pos);
-        dev_free(d_row_base);
         *out = p;
         return LB_OK;
     }
     // Synchronous copies: the host vectors die at return.
     if ((e = cudaMemcpy(d_ro_pos, ro_pos.data(), kc * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(d_row_base, row_base.data(), (kc + 1) * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->mat_row_base, row_base.data(), (kc + 1) * sizeof(int), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
         (e = cudaMemcpy(p->mat_nz_base, nz_base.data(), (kc + 1) * sizeof(int), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
         (e = cudaMemcpy(p->mat_col_base, col_base.data(), kc * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
-    e = launch_block_diag_offsets(kc, d_ro_pos, d_row_base, p->mat_nz_base, row_offsets_concat,
+    e = launch_block_diag_offsets(kc, d_ro_pos, p->mat_row_base, p->mat_nz_base, row_offsets_concat,
                                   static_cast<int>(rows), p->ro_g, stream);
     if (e == cudaSuccess)
         e = launch_partition(static_cast<int>(rows), nnz, p->ro_g, p->tile_items, p->tile_row, p->tile_nz, stream);
@@ -840,8 +846,13 @@ lb_status lb_batched_plan_create(int count, const int *h_m, const int *h_n, cons
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the index scratch is freed below
     if (e != cudaSuccess) return fail(e);
     dev_free(d_ro_pos);
-    dev_free(d_row_base);
     *out = p;
+    return LB_OK;
+}
+
+lb_status lb_batched_plan_schedule(const lb_batched_plan *p, lb_schedule *s) {
+    if (!p || !s) return LB_ERR_INVALID_ARG;
+    *s = p->sched;
     return LB_OK;
 }
 
@@ -878,6 +889,14 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, c
     if (!aligned(col_idx_concat, 4) || !aligned(values_concat, value_bytes(vdt)) || !aligned(x_concat, 4) ||
         !aligned(y_concat, 4))
         return LB_ERR_INVALID_ARG;
+    if (p->sched == LB_SCHED_THREAD_MAPPED) {
+        if (g_ev_before) cudaEventRecord(g_ev_before, stream);
+        const cudaError_t e = launch_batched_rows(vdt, p->total_rows, p->ro_g, col_idx_concat, values_concat, x_concat,
+                                                  p->total_cols, y_concat, p->kc, p->mat_row_base, p->mat_col_base,
+                                                  p->G, p->tile_row, stream);
+        if (g_ev_after) cudaEventRecord(g_ev_after, stream);
+        return from_cuda(e);
+    }
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
     MergeArgs a{};
@@ -905,7 +924,8 @@ lb_status lb_spmv_batched(const lb_batched_plan *p, const int *col_idx_concat, c
 
 void lb_batched_plan_destroy(lb_batched_plan *p) {
     if (!p) return;
-    int *ints[] = {p->ro_g, p->mat_nz_base, p->mat_col_base, p->tile_row, p->tile_nz, p->tile_mat, p->carry_row};
+    int *ints[] = {p->ro_g,    p->mat_nz_base, p->mat_col_base, p->mat_row_base,
+                   p->tile_row, p->tile_nz,     p->tile_mat,     p->carry_row};
     for (int *q : ints)
         if (q) dev_free(q);
     if (p->carry_val) dev_free(p->carry_val);

@@ -176,6 +176,11 @@ cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_it
                                         const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream);
 
 // Batched-plan helpers.
+// Thread-mapped SpMV over a batch's block-diagonal matrix (rows longer than a few nonzeros
+// summed by the warp); every row is complete when the kernel ends (no fixup).
+cudaError_t launch_batched_rows(lb_dtype vdt, long long rows, const int *ro, const int *ci, const void *val,
+                                const float *x, long long x_len, float *y, int kc, const int *mat_row_base,
+                                const int *mat_col_base, int G, const int *tile_row, cudaStream_t stream);
 cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *row_base, const int *nz_base,
                                       const int *ro_concat, int total_rows, int *ro_global, cudaStream_t stream);
 cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, const int *mat_nz_base,

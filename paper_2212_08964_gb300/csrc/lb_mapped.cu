@@ -259,4 +259,160 @@ cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------------------------------
+// Thread-mapped over a batch (the row schedule of Ch.3 Sec. "Thread-Mapped", applied to the
+// block-diagonal matrix of a batched plan), with the group-mapped remedy for its imbalance:
+// a row longer than kLongRow nonzeros is not left to one lane but summed by the whole warp
+// (Ch.3 Sec. "Group-Mapped" with the group a warp).  Each warp owns a contiguous range of
+// rows, 32 at a time with consecutive rows on consecutive lanes; a lane sums its short row
+// in order with compensated addition; the warp then takes the chunk's long rows one by one,
+// each lane summing a strided share and a fixed shuffle tree joining them.  Every row is
+// finished by one lane or one warp: no carries and no fixup.  The warps' row ranges come
+// from the plan's merge-path partition (whole runs of its tiles, cut at the row ends the
+// tiles' boundaries fall after), so each warp gets about the same rows + nonzeros.  The matrix
+// of a row (for its column base) is found once per warp by binary search and then followed
+// forward.
+
+struct BatchRowsArgs {
+    long long rows;           // rows of the block-diagonal matrix
+    const int *ro;            // its offsets [rows + 1]
+    const int *ci;            // local column indices (per matrix)
+    const void *val;          // values
+    const float *x;           // concatenated x
+    long long x_len;          // its length
+    float *y;                 // concatenated y [rows]
+    int kc;                   // matrices with rows
+    const int *mat_row_base;  // [kc + 1] first global row of each matrix
+    const int *mat_col_base;  // [kc] offset of each matrix's x inside x
+    int G;                    // merge-path tiles of the plan's partition
+    const int *tile_row;      // [G + 1] row ends consumed before each tile boundary
+};
+
+constexpr int kLongRow = 32;
+
+template <typename V>
+__global__ void __launch_bounds__(256) batched_rows_kernel(const BatchRowsArgs a) {
+    const V *__restrict__ v = static_cast<const V *>(a.val);
+    const int lane = threadIdx.x & 31;
+    const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    const long long per = (a.G + nwarps - 1) / nwarps;  // tiles per warp
+    const long long t0 = warp * per, t1 = t0 + per < a.G ? t0 + per : a.G;
+    if (t0 >= t1) return;
+    const long long r_begin = __ldg(a.tile_row + t0);
+    const long long r_end = t1 == a.G ? a.rows : __ldg(a.tile_row + t1);
+    long long c = 0;  // chunks of 32 rows from r_begin
+    const long long c_end = (r_end - r_begin + 31) >> 5;
+    if (c >= c_end) return;
+    // Matrix of the warp's first row: the last i with mat_row_base[i] <= row.
+    int mi = 0;
+    if (lane == 0) {
+        int lo = 0, hi = a.kc - 1;
+        const long long r = r_begin;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.mat_row_base + mid) <= r)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        mi = lo;
+    }
+    mi = __shfl_sync(0xffffffffu, mi, 0);
+    // Row offsets of the first chunk; each chunk loads the next chunk's while it works.
+    auto load_ro = [&](long long cc, int &s, int &e) {
+        const long long row = r_begin + (cc << 5) + lane;
+        s = row < r_end ? __ldg(a.ro + row) : 0;
+        e = row < r_end ? __ldg(a.ro + row + 1) : 0;
+    };
+    int s, e;
+    load_ro(c, s, e);
+    for (; c < c_end; ++c) {
+        const long long row = r_begin + (c << 5) + lane;
+        const bool in = row < r_end;
+        int i = mi;
+        if (in)
+            while (i + 1 < a.kc && __ldg(a.mat_row_base + i + 1) <= row) ++i;
+        mi = __shfl_sync(0xffffffffu, i, 31);  // rows only increase
+        const int cb = in ? __ldg(a.mat_col_base + i) : 0;
+        const bool lng = e - s > kLongRow;
+        int ns = 0, ne = 0;
+        if (c + 1 < c_end) load_ro(c + 1, ns, ne);
+        // A short row: its lane sums it in order, two nonzeros' loads in flight at a time.
+        float acc = 0.f, comp = 0.f;
+        if (in && !lng) {
+            int k = s;
+            for (; k + 1 < e; k += 2) {
+                const long long g0 = static_cast<long long>(__ldg(a.ci + k)) + cb;
+                const long long g1 = static_cast<long long>(__ldg(a.ci + k + 1)) + cb;
+                const float v0 = to_f32(__ldg(v + k)), v1 = to_f32(__ldg(v + k + 1));
+                const float x0 = LB_IN_RANGE(g0, a.x_len) ? __ldg(a.x + g0) : 0.f;
+                const float x1 = LB_IN_RANGE(g1, a.x_len) ? __ldg(a.x + g1) : 0.f;
+                kbn_add(acc, comp, v0 * x0);
+                kbn_add(acc, comp, v1 * x1);
+            }
+            if (k < e) {
+                const long long g0 = static_cast<long long>(__ldg(a.ci + k)) + cb;
+                if (LB_IN_RANGE(g0, a.x_len)) kbn_add(acc, comp, to_f32(__ldg(v + k)) * __ldg(a.x + g0));
+            }
+        }
+        // Long rows: the whole warp, one row at a time, 128 nonzeros per step.
+        for (unsigned lm = __ballot_sync(0xffffffffu, in && lng); lm; lm &= lm - 1) {
+            const int src = __ffs(lm) - 1;
+            const int rs = __shfl_sync(0xffffffffu, s, src), re = __shfl_sync(0xffffffffu, e, src);
+            const int rcb = __shfl_sync(0xffffffffu, cb, src);
+            float ps = 0.f, pc = 0.f;
+            for (int k0 = rs; k0 < re; k0 += 128) {
+                int kc4[4];
+                float vv4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k0 + 32 * u + lane;
+                    kc4[u] = k < re ? __ldg(a.ci + k) : -1;
+                    vv4[u] = k < re ? to_f32(__ldg(v + k)) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long gcol = static_cast<long long>(kc4[u]) + rcb;
+                    if (kc4[u] >= 0 && LB_IN_RANGE(gcol, a.x_len)) kbn_add(ps, pc, vv4[u] * __ldg(a.x + gcol));
+                }
+            }
+            float t = ps + pc;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == src) acc = t, comp = 0.f;
+        }
+        if (in) a.y[row] = acc + comp;
+        s = ns;
+        e = ne;
+    }
+}
+
+cudaError_t launch_batched_rows(lb_dtype vdt, long long rows, const int *ro, const int *ci, const void *val,
+                                const float *x, long long x_len, float *y, int kc, const int *mat_row_base,
+                                const int *mat_col_base, int G, const int *tile_row, cudaStream_t stream) {
+    if (rows <= 0 || kc <= 0 || G <= 0) return cudaSuccess;
+    BatchRowsArgs a{rows, ro, ci, val, x, x_len, y, kc, mat_row_base, mat_col_base, G, tile_row};
+    // One wave of resident warps, each a contiguous run of tiles.
+    auto wave = [&](auto kern) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        long long blocks = static_cast<long long>(per_sm) * current_sm_count();
+        const long long need = (static_cast<long long>(G) + 7) / 8;  // 8 warps per block, a tile or more each
+        if (blocks > need) blocks = need;
+        kern<<<static_cast<int>(blocks), 256, 0, stream>>>(a);
+        return cudaGetLastError();
+    };
+    switch (vdt) {
+        case LB_F32:
+            return wave(batched_rows_kernel<float>);
+        case LB_BF16:
+            return wave(batched_rows_kernel<__nv_bfloat16>);
+        case LB_F16:
+            return wave(batched_rows_kernel<__half>);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace lb

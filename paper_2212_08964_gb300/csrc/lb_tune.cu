@@ -100,8 +100,11 @@ extern "C" lb_status lb_tune_batched(int count_m, const int *h_m, const int *h_n
         !x_concat || !y_concat)
         return LB_ERR_INVALID_ARG;
     std::vector<lb_tune_result> out;
-    for (const Candidate &c : all_candidates()) {
-        if (c.s != LB_SCHED_MERGE_PATH) continue;  // batches run as one merge path
+    std::vector<Candidate> cands;
+    cands.push_back({LB_SCHED_THREAD_MAPPED, lb_tuning{0, 0, 0}});
+    for (const Candidate &c : all_candidates())
+        if (c.s == LB_SCHED_MERGE_PATH) cands.push_back(c);  // the batch schedules: rows, or one merge path
+    for (const Candidate &c : cands) {
         lb_batched_plan *p = nullptr;
         lb_status st = lb_batched_plan_create(count_m, h_m, h_n, h_nnz, row_offsets_concat, c.s, &c.t, stream, &p);
         if (st != LB_OK) return st;

@@ -129,6 +129,7 @@ def _declare(lib):
         "lb_batched_plan_create": [_I, _P, _P, _P, _P, _I, ctypes.POINTER(_Tuning), _P, ctypes.POINTER(_P)],
         "lb_batched_plan_partition": [_P, _P, _P, ctypes.POINTER(_I)],
         "lb_batched_plan_info": [_P, ctypes.POINTER(_Tuning), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+        "lb_batched_plan_schedule": [_P, ctypes.POINTER(_I)],
         "lb_spmv_batched": [_P, _P, _P, _I, _P, _P, _P],
         "lb_validate_csr": [_I, _I, _I, _P, _P, _I, _P, _P],
         "lb_device_error": [ctypes.POINTER(_I), _I],
@@ -478,10 +479,12 @@ class CscPlan:
 
 
 class BatchedPlan:
-    """K CSR matrices run as one block-diagonal matrix in one persistent launch."""
+    """K CSR matrices run as one block-diagonal matrix in one launch: the global merge path
+    (``schedule="merge_path"``, with the fixup) or a row per lane with long rows summed by
+    the warp (``schedule="thread_mapped"``, no fixup)."""
 
     def __init__(self, ms, ns, nnzs, row_offsets_concat: torch.Tensor, threads: int = 0, items_per_thread: int = 0,
-                 stream=None):
+                 stream=None, schedule: str = "merge_path"):
         lib = ensure_loaded()
         _need(row_offsets_concat, torch.int32, "row_offsets_concat")
         self.ms = np.ascontiguousarray(ms, np.int32)
@@ -495,7 +498,7 @@ class BatchedPlan:
         t = _tuning(threads, items_per_thread, 0)
         _check(
             lib.lb_batched_plan_create(self.count, self.ms.ctypes.data, self.ns.ctypes.data, self.nnzs.ctypes.data,
-                                       _ptr(row_offsets_concat), SCHEDULES["merge_path"], ctypes.byref(t), _stream(stream),
+                                       _ptr(row_offsets_concat), SCHEDULES[schedule], ctypes.byref(t), _stream(stream),
                                        ctypes.byref(self._h)),
             "lb_batched_plan_create",
         )
@@ -503,7 +506,10 @@ class BatchedPlan:
     def info(self) -> dict:
         t, g, ti = _Tuning(), _I(), _I()
         _check(_lib.lb_batched_plan_info(self._h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(ti)), "lb_batched_plan_info")
-        return {"threads": t.threads, "items_per_thread": t.items_per_thread, "num_tiles": g.value, "tile_items": ti.value}
+        s = _I()
+        _check(_lib.lb_batched_plan_schedule(self._h, ctypes.byref(s)), "lb_batched_plan_schedule")
+        return {"schedule": _SCHED_NAMES[s.value], "threads": t.threads, "items_per_thread": t.items_per_thread,
+                "num_tiles": g.value, "tile_items": ti.value}
 
     def partition(self):
         g = _I()

@@ -265,6 +265,32 @@ def batched_powerlaw(count: int, m_lo: int, m_hi: int, nnz_target: float, s: flo
     )
 
 
+def stencil5_csr(k: int, rng: np.random.Generator) -> CSR:
+    """5-point 2-D Laplacian pattern on a k x k grid (natural ordering, sorted columns),
+    every stored entry uniform on [-1, 1]."""
+    m = k * k
+    r = np.arange(m, dtype=np.int64)
+    i, j = r // k, r % k
+    offs = [(-k, i > 0), (-1, j > 0), (0, np.ones(m, bool)), (1, j < k - 1), (k, i < k - 1)]
+    present = np.stack([p for _, p in offs], axis=1)
+    cols = r[:, None] + np.array([o for o, _ in offs], dtype=np.int64)[None, :]
+    ro = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(present.sum(axis=1), out=ro[1:])
+    return CSR(m, m, ro.astype(np.int32), cols[present].astype(np.int32), uniform_pm1(rng, int(ro[-1])))
+
+
+def batched_grid(count: int, k_lo: int, k_hi: int, seed: int) -> BatchedCSR:
+    """``count`` 5-point Laplacians on k x k grids, k log-uniform in [k_lo, k_hi]: a batch of
+    regular matrices of uneven size (a batch of small PDE problems)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ks = np.clip(np.floor(np.exp(rng.uniform(math.log(k_lo), math.log(k_hi + 1), size=count))), k_lo, k_hi)
+    mats = [stencil5_csr(int(k), rng) for k in ks.astype(np.int64)]
+    ms = np.array([a.m for a in mats], dtype=np.int64)
+    return BatchedCSR(ms, ms.copy(), np.array([a.nnz for a in mats], dtype=np.int64),
+                      np.concatenate([a.row_offsets for a in mats]), np.concatenate([a.col_idx for a in mats]),
+                      np.concatenate([a.values for a in mats]))
+
+
 def from_dense(a: np.ndarray) -> CSR:
     """CSR of the nonzero pattern of a small dense matrix (row-major scan)."""
     a = np.asarray(a, dtype=np.float32)
@@ -284,6 +310,9 @@ WORKLOADS = {
     "lognormal_1m": dict(kind="lognormal", m=1_048_576, n=1_048_576, mu=2.5, sigma=1.2, seed=4),
     "batched_4096": dict(kind="batched", count=4096, m_lo=64, m_hi=65536, nnz=50_000_000, s=1.5, seed=5),
     "powerlaw_8m": dict(kind="powerlaw", m=8_388_608, n=8_388_608, nnz=128_000_000, s=1.3, l_max=500_000, seed=6),
+    # A second batch class: 1024 2-D Laplacians of uneven size (m_i = k^2, k log-uniform in
+    # [8, 256], so m_i spans [64, 65536] as in batched_4096), about 48M nonzeros.
+    "batched_grid_1024": dict(kind="batched_grid", count=1024, k_lo=8, k_hi=256, seed=7),
 }
 
 
@@ -302,6 +331,9 @@ def workload(name: str, scale: float = 1.0):
     if kind == "stencil":
         nx = max(2, int(round(w["nx"] * scale ** (1.0 / 3.0))))
         return stencil7_csr(nx, w["seed"])
+    if kind == "batched_grid":
+        count = max(1, int(w["count"] * scale))
+        return batched_grid(count, w["k_lo"], w["k_hi"], w["seed"])
     if kind == "batched":
         count = max(1, int(w["count"] * scale))
         return batched_powerlaw(count, w["m_lo"], w["m_hi"], w["nnz"] * count / w["count"], w["s"], w["seed"])

@@ -72,7 +72,7 @@ def test_host_side_argument_rejection(lib):
     assert lib.lb_plan_create(4, 4, 4, ctypes.c_void_p(16), 4, ctypes.byref(bad_group), None, ctypes.byref(out)) == -1
     assert lib.lb_batched_plan_create(1, None, None, None, None, 1, None, None, ctypes.byref(out)) == -1
     one = (ctypes.c_int * 1)(4)
-    assert lib.lb_batched_plan_create(1, one, one, one, ctypes.c_void_p(16), 1, None, None, ctypes.byref(out)) == -3
+    assert lib.lb_batched_plan_create(1, one, one, one, ctypes.c_void_p(16), 2, None, None, ctypes.byref(out)) == -3
     assert lib.lb_spmv_planned(None, None, None, 0, None, None, None) == -1
     assert lib.lb_spmv_t(None, None, 0, None, None, None) == -1
     assert lib.lb_spmv_dvalues(None, None, None, None, None, None) == -1

@@ -107,10 +107,11 @@ def test_tune_batched(lb, orc):
     t = autotune.Table()
     res = autotune.tune_batched(b.ms, b.ns, b.nnzs, dev(b.row_offsets), dev(b.col_idx), dev(b.values), dev(x),
                                 reps=3, table=t)
-    assert len(res) == 5 and all(r["schedule"] == "merge_path" for r in res)
+    assert len(res) == 6
+    assert sorted({r["schedule"] for r in res}) == ["merge_path", "thread_mapped"]
     best = res[0]
-    plan = lb.BatchedPlan(b.ms, b.ns, b.nnzs, dev(b.row_offsets), threads=best["threads"],
-                          items_per_thread=best["items_per_thread"])
+    plan = autotune.batched_plan_for(b.ms, b.ns, b.nnzs, dev(b.row_offsets), t)
+    assert plan.info()["schedule"] == best["schedule"]
     y = plan.spmv(dev(b.col_idx), dev(b.values), dev(x))
     torch.cuda.synchronize()
     check_bound(y.cpu().numpy(), orc.batched_spmv(b, x), orc.batched_row_absdot(b, x), 1e-5)

@@ -1,5 +1,7 @@
-"""Batched SpMV (many matrices, one persistent launch) vs per-matrix oracle runs; the global
-partition bit-exact against the block-diagonal counting definition; CUDA-graph replay."""
+"""Batched SpMV (many matrices, one launch) vs per-matrix oracle runs, under both batch
+schedules (the global merge path, and thread-mapped rows with long rows summed by the warp);
+the global partition bit-exact against the block-diagonal counting definition; CUDA-graph
+replay."""
 import numpy as np
 import pytest
 import torch
@@ -52,11 +54,13 @@ def test_batched_partition_bit_exact(lb, orc, shape):
     assert np.array_equal(tr, otr) and np.array_equal(tn, otn)
 
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_batched_vs_oracle(lb, orc, dtype):
+@pytest.mark.parametrize("schedule", ["merge_path", "thread_mapped"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_batched_vs_oracle(lb, orc, dtype, schedule):
     b = _batch_with_degenerates()
     x = vec(int(b.ns.sum()), 301)
-    plan = _plan(lb, b)
+    plan = _plan(lb, b, schedule=schedule)
+    assert plan.info()["schedule"] == schedule
     y = plan.spmv(dev(b.col_idx), dev(b.values, dtype), dev(x))
     torch.cuda.synchronize()
     vals = b.values if dtype == torch.float32 else torch.from_numpy(b.values).to(dtype).float().numpy()
@@ -66,10 +70,11 @@ def test_batched_vs_oracle(lb, orc, dtype):
     check_bound(y.cpu().numpy(), ref, scale, TOL32)
 
 
-def test_batched_cuda_graph_replay(lb, orc):
+@pytest.mark.parametrize("schedule", ["merge_path", "thread_mapped"])
+def test_batched_cuda_graph_replay(lb, orc, schedule):
     b = workload("batched_4096", 0.05)
     x = vec(int(b.ns.sum()), 302)
-    plan = _plan(lb, b)
+    plan = _plan(lb, b, schedule=schedule)
     ci, v, xd = dev(b.col_idx), dev(b.values), dev(x)
     y = torch.empty(int(b.ms.sum()), device="cuda")
     s = torch.cuda.Stream()
@@ -91,16 +96,46 @@ def test_batched_cuda_graph_replay(lb, orc):
     assert torch.equal(y, y1)
 
 
-def test_full_size_batched_4096(lb, orc):
+@pytest.mark.parametrize("schedule", ["merge_path", "thread_mapped"])
+def test_full_size_batched_4096(lb, orc, schedule):
     b = workload("batched_4096")
     x = vec(int(b.ns.sum()), 5)
-    plan = _plan(lb, b)
+    plan = _plan(lb, b, schedule=schedule)
     y = plan.spmv(dev(b.col_idx), dev(b.values), dev(x))
     torch.cuda.synchronize()
     ref = orc.batched_spmv(b, x)
     mx, med = check_bound(y.cpu().numpy(), ref, orc.batched_row_absdot(b, x), TOL32)
-    print(f"batched_4096: max rel err {mx:.3e} median {med:.3e}")
+    print(f"batched_4096 {schedule}: max rel err {mx:.3e} median {med:.3e}")
     ro_g = orc.block_diagonal_offsets(b.ms, b.nnzs, b.row_offsets)
     tr, tn = plan.partition()
     otr, otn = orc.partition(ro_g, plan.info()["tile_items"])
     assert np.array_equal(tr, otr) and np.array_equal(tn, otn)
+
+
+def test_thread_mapped_batch_long_rows_and_single_matrix(lb, orc):
+    """Rows far longer than the warp's share (summed by the whole warp), next to rows of one
+    nonzero and empty rows, in a batch of one matrix and in a batch of many."""
+    rng = np.random.default_rng(23)
+    lens = np.concatenate([rng.integers(0, 3, 200), [5000, 33, 9, 8, 0, 70000], rng.integers(0, 3, 100)])
+    one = synth.csr_from_row_lengths(rng, 80_000, lens)
+    for mats in ([one], [one, synth.csr_from_row_lengths(rng, 50, rng.integers(0, 12, 700)), one]):
+        b = synth.BatchedCSR(
+            np.array([a.m for a in mats], np.int64), np.array([a.n for a in mats], np.int64),
+            np.array([a.nnz for a in mats], np.int64), np.concatenate([a.row_offsets for a in mats]),
+            np.concatenate([a.col_idx for a in mats]), np.concatenate([a.values for a in mats]))
+        x = vec(int(b.ns.sum()), 303)
+        plan = _plan(lb, b, schedule="thread_mapped")
+        y = plan.spmv(dev(b.col_idx), dev(b.values), dev(x))
+        torch.cuda.synchronize()
+        check_bound(y.cpu().numpy(), orc.batched_spmv(b, x), orc.batched_row_absdot(b, x), TOL32)
+
+
+@pytest.mark.parametrize("schedule", ["merge_path", "thread_mapped"])
+def test_batched_grid(lb, orc, schedule):
+    """The batch of 2-D Laplacians of uneven size (regular short rows) under both schedules."""
+    b = workload("batched_grid_1024", 0.1)
+    x = vec(int(b.ns.sum()), 304)
+    plan = _plan(lb, b, schedule=schedule)
+    y = plan.spmv(dev(b.col_idx), dev(b.values), dev(x))
+    torch.cuda.synchronize()
+    check_bound(y.cpu().numpy(), orc.batched_spmv(b, x), orc.batched_row_absdot(b, x), TOL32)
