@@ -178,10 +178,16 @@ def test_static_allocates_nothing(lb):
     assert rt.cudaMemPoolSetAttribute(pool, _POOL_USED_HIGH, ctypes.byref(zero)) == 0  # reset to current use
     used0 = _pool_attr(rt, pool, _POOL_USED_CURRENT)
     free0 = torch.cuda.mem_get_info()[0]
-    for y in ys:
-        assert lib.lb_spmv_static(a.m, a.n, a.nnz, p(ro), p(ci), p(v), 0, p(x), p(y), stream) == 0
-    torch.cuda.synchronize()
+    live0 = lb.live_allocations()
+    lb.fail_allocations_after(0)  # any allocation through the library's own allocator would now fail
+    try:
+        for y in ys:
+            assert lib.lb_spmv_static(a.m, a.n, a.nnz, p(ro), p(ci), p(v), 0, p(x), p(y), stream) == 0
+        torch.cuda.synchronize()
+    finally:
+        lb.fail_allocations_after(-1)
     assert _pool_attr(rt, pool, _POOL_USED_HIGH) == used0
     assert torch.cuda.mem_get_info()[0] == free0
+    assert lb.live_allocations() == live0
     assert torch.equal(ys[0], ys[1])
     _device_error_clear(lb)
