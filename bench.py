@@ -92,7 +92,7 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash(files=("lb_merge.cuh", "lb_internal.cuh")) -> str:
+def kernel_source_hash(files=("lb_merge.cuh", "lb_warp.cuh", "lb_internal.cuh")) -> str:
     """Hash of a kernel's source files with comments and blank space removed, so a recorded
     DRAM-traffic figure is used only while the code it was measured on is unchanged."""
     h = hashlib.sha256()
