@@ -222,6 +222,10 @@ struct lb_plan {
     int *mm_carry_row = nullptr;
     float *mm_carry_val = nullptr;
     long long mm_cols = 0;
+    long long mm_carry_tiles = 0;
+    // SpMM's 248-item warp tiles, for plans whose warp tiles have another size (made on first use).
+    int *mm_tile_row = nullptr, *mm_tile_nz = nullptr;
+    int mmG = 0;
 };
 
 struct lb_batched_plan {
@@ -261,9 +265,14 @@ static void free_plan_arrays(lb_plan *p) {
     p->nz_carry_val = nullptr;
     if (p->mm_carry_row) dev_free(p->mm_carry_row);
     if (p->mm_carry_val) dev_free(p->mm_carry_val);
+    if (p->mm_tile_row) dev_free(p->mm_tile_row);
+    if (p->mm_tile_nz) dev_free(p->mm_tile_nz);
+    p->mm_tile_row = p->mm_tile_nz = nullptr;
+    p->mmG = 0;
     p->mm_carry_row = nullptr;
     p->mm_carry_val = nullptr;
     p->mm_cols = 0;
+    p->mm_carry_tiles = 0;
     int *ints[] = {p->ro, p->tile_row, p->tile_nz, p->carry_row, p->w_tile_row, p->w_tile_nz, p->w_carry_row};
     for (int *q : ints)
         if (q) dev_free(q);
@@ -729,21 +738,59 @@ lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     const size_t c_bytes = static_cast<size_t>(p->m) * static_cast<size_t>(kc) * sizeof(float);
     if (p->nnz == 0) return from_cuda(cudaMemsetAsync(C, 0, c_bytes, stream));
-    if (p->tile_items > 2048) return LB_ERR_UNSUPPORTED;  // SpMM stages tiles of up to 2048 items
-    if (kc > p->mm_cols) {
-        // Carries for G tiles of kc columns; allocated once per plan and column count growth.
+    if (!aligned(col_idx, 4) || !aligned(values, value_bytes(vdt)) || !aligned(B, 4) || !aligned(C, 4))
+        return LB_ERR_INVALID_ARG;
+    int *err = device_error_word();
+    if (!err) return LB_ERR_CUDA;
+    // kc <= 4: the warp-tiled kernel over 248-item warp tiles (the plan's own when they have
+    // that size, else a partition of its own, made on the first call that needs it).  Wider
+    // B: the block kernel over the plan's block tiles.
+    const bool warp = kc <= 4;
+    const int *tr = p->tile_row, *tn = p->tile_nz;
+    int G = p->G;
+    if (warp) {
+        const int T = spmm_warp_tile_items();
+        tr = p->w_tile_row, tn = p->w_tile_nz, G = p->wG;
+        if (p->w_tile_items != T) {
+            if (!p->mm_tile_row) {
+                const int g = num_tiles_of(p->m, p->nnz, T);
+                cudaError_t e = dmalloc(&p->mm_tile_row, static_cast<size_t>(g) + 1);
+                if (e == cudaSuccess) e = dmalloc(&p->mm_tile_nz, static_cast<size_t>(g) + 1);
+                if (e == cudaSuccess) e = launch_partition(p->m, p->nnz, p->ro, T, p->mm_tile_row, p->mm_tile_nz, stream);
+                if (e != cudaSuccess) {
+                    if (p->mm_tile_row) dev_free(p->mm_tile_row);
+                    if (p->mm_tile_nz) dev_free(p->mm_tile_nz);
+                    p->mm_tile_row = p->mm_tile_nz = nullptr;
+                    return from_cuda(e);
+                }
+                p->mmG = g;
+            }
+            tr = p->mm_tile_row, tn = p->mm_tile_nz, G = p->mmG;
+        }
+    } else if (p->tile_items > 2048) {
+        return LB_ERR_UNSUPPORTED;  // the block kernel stages tiles of up to 2048 items
+    }
+    if (kc > p->mm_cols || G > p->mm_carry_tiles) {
+        // Carries for G tiles of kc columns; reallocated only when either grows.
+        const long long cols = kc > p->mm_cols ? kc : p->mm_cols;
+        const long long tiles = G > p->mm_carry_tiles ? G : p->mm_carry_tiles;
         if (p->mm_carry_row) dev_free(p->mm_carry_row);
         if (p->mm_carry_val) dev_free(p->mm_carry_val);
         p->mm_carry_row = nullptr;
         p->mm_carry_val = nullptr;
         p->mm_cols = 0;
-        cudaError_t e = dmalloc(&p->mm_carry_row, static_cast<size_t>(p->G));
-        if (e == cudaSuccess) e = dmalloc(&p->mm_carry_val, static_cast<size_t>(p->G) * static_cast<size_t>(kc));
+        p->mm_carry_tiles = 0;
+        cudaError_t e = dmalloc(&p->mm_carry_row, static_cast<size_t>(tiles));
+        if (e == cudaSuccess) e = dmalloc(&p->mm_carry_val, static_cast<size_t>(tiles) * static_cast<size_t>(cols));
         if (e != cudaSuccess) return from_cuda(e);
-        p->mm_cols = kc;
+        p->mm_cols = cols;
+        p->mm_carry_tiles = tiles;
     }
-    return from_cuda(launch_spmm(vdt, p->G, p->m, p->n, kc, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx,
-                                 values, B, C, p->mm_carry_row, p->mm_carry_val, stream));
+    if (warp)
+        return from_cuda(launch_spmm_warp(vdt, G, p->m, p->n, p->nnz, kc, tr, tn, p->ro + 1, col_idx, values, B, C,
+                                          p->mm_carry_row, p->mm_carry_val, err, stream));
+    return from_cuda(launch_spmm_block(vdt, G, p->m, p->n, kc, p->tile_items, tr, tn, p->ro + 1, col_idx, values, B, C,
+                                       p->mm_carry_row, p->mm_carry_val, stream));
 }
 
 void lb_plan_destroy(lb_plan *p) {

@@ -186,11 +186,17 @@ cudaError_t launch_block_diag_offsets(int count, const int *ro_pos, const int *r
 cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, const int *mat_nz_base,
                                int *tile_mat, cudaStream_t stream);
 
-// SpMM C = A B (B dense n x kc row-major, C m x kc) over the forward partition (tiles of at
-// most 2048 items), then the fixup of the carries (carry_row[G], carry_val[G * kc]).
-cudaError_t launch_spmm(lb_dtype vdt, int G, int m, int n, int kc, int tile_items, const int *tile_row, const int *tile_nz,
-                        const int *row_end, const int *ci, const void *values, const float *B, float *C,
-                        int *carry_row, float *carry_val, cudaStream_t st);
+// SpMM C = A B (B dense n x kc row-major, C m x kc), then the fixup of the carries
+// (carry_row[G], carry_val[G * kc]).  kc <= 4: over warp tiles of spmm_warp_tile_items() items
+// (a tile that fails the tile check records LB_ERR_BAD_MATRIX in err).  Otherwise: over block
+// tiles of at most 2048 items.
+int spmm_warp_tile_items();
+cudaError_t launch_spmm_warp(lb_dtype vdt, int G, int m, int n, int nnz, int kc, const int *tile_row,
+                             const int *tile_nz, const int *row_end, const int *ci, const void *values, const float *B,
+                             float *C, int *carry_row, float *carry_val, int *err, cudaStream_t st);
+cudaError_t launch_spmm_block(lb_dtype vdt, int G, int m, int n, int kc, int tile_items, const int *tile_row,
+                              const int *tile_nz, const int *row_end, const int *ci, const void *values,
+                              const float *B, float *C, int *carry_row, float *carry_val, cudaStream_t st);
 
 // Nonzero splitting: tiles of nzsplit_tile_nonzeros() nonzeros; first_row / last_row[G] hold
 // the rows of each tile's first and last nonzero; the SpMV clears y, writes rows with nonzeros

@@ -15,8 +15,8 @@ TOL32 = 1e-5
 
 
 def _long_rows():
-    """Power-law body plus rows of 5k-20k nonzeros (each spans several 2040-item tiles) and
-    runs of empty rows."""
+    """Power-law body plus rows of 5k-20k nonzeros (each spans 20-80 warp tiles of 248
+    items, more than one 32-tile probe of the fixup) and runs of empty rows."""
     rng = np.random.default_rng(71)
     lengths = rng.integers(0, 12, 6000)
     lengths[[5, 6, 7, 3000, 5999]] = [20000, 0, 9000, 5000, 12000]
@@ -98,3 +98,20 @@ def test_spmm_large_powerlaw(lb, orc):
     torch.cuda.synchronize()
     _check(C.cpu().numpy(), orc.spmm(a.row_offsets, a.col_idx, a.values, B),
            orc.spmm_absdot(a.row_offsets, a.col_idx, a.values, B), TOL32)
+
+
+@pytest.mark.parametrize("shape,kc", [((128, 16), 2), ((128, 16), 4), ((512, 8), 3), ((128, 16), 8), ((128, 16), 12)])
+def test_spmm_other_plan_shapes(lb, orc, shape, kc):
+    """Plans of other merge-path shapes.  kc <= 4 runs over 248-item warp tiles: a partition of
+    its own, built on the first call, for plans whose warp tiles differ (128 x 16), else the
+    plan's (512 x 8).  Wider B runs over the plan's block tiles."""
+    a = _long_rows()
+    ro, ci, v = to_dev(a)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path", threads=shape[0], items_per_thread=shape[1])
+    B = np.random.default_rng(kc + 100).uniform(-1, 1, (a.n, kc)).astype(np.float32)
+    for _ in range(2):
+        C = plan.spmm(ci, v, dev(B))
+        torch.cuda.synchronize()
+        _check(C.cpu().numpy(), orc.spmm(a.row_offsets, a.col_idx, a.values, B),
+               orc.spmm_absdot(a.row_offsets, a.col_idx, a.values, B), TOL32)
+    assert lb.device_error() == 0
