@@ -168,8 +168,18 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
                 hi = new_hi;
             }
             const long long end = hi;  // carries [cs, end) belong to row rs
+            // Eight loads in flight per lane: a row over thousands of tiles is summed in a few
+            // memory latencies instead of one per 32 carries.
             float sum = 0.f, comp = 0.f;
-            for (long long q = cs + lane; q < end; q += 32) kbn_add(sum, comp, __ldg(carry_val + q));
+            long long q = cs + lane;
+            for (; q + 7 * 32 < end; q += 8 * 32) {
+                float u[8];
+#pragma unroll
+                for (int h = 0; h < 8; ++h) u[h] = __ldg(carry_val + q + 32 * h);
+#pragma unroll
+                for (int h = 0; h < 8; ++h) kbn_add(sum, comp, u[h]);
+            }
+            for (; q < end; q += 32) kbn_add(sum, comp, __ldg(carry_val + q));
             float v = sum + comp;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
