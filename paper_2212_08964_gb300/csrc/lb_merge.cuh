@@ -266,35 +266,63 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
         const int e0 = kb + IPT * lane;
         const uint32_t vm = ok ? slot_mask<IPT>(e0, cur.k0, cur.k1) : 0u;
 
-        // 1. This tile's gathers.
-        float xv[IPT];
-#pragma unroll
-        for (int q = 0; q < IPT; ++q)
-            xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) ? __ldg(a.x + col[q]) : 0.f;
-
-        // 2. The next tile's indices (and the bounds of the one after) while they are in flight.
         const bool has_next = t + nw < G;
         const WBounds nxt = bounds_bcast<MODE>(bw_next);
-        if (has_next) {
-            load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
-            bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
-        }
-
-        if (!ok) {
-            if (lane == 0) {
-                atomicExch(a.err, static_cast<int>(LB_ERR_BAD_MATRIX));
-                a.carry_row[t] = -1;  // the fixup skips it
-                a.carry_val[t] = 0.f;
-            }
-            cur = nxt;
-            continue;
-        }
-
-        // 3. Values, and the row starts found from the row ends, while the gathers are in flight.
-        float p[IPT];
-        load_vals<V, IPT, MODE>(a, e0, vm, pol, p);
+        float p[IPT], xv[IPT];
         int e_first, e_last;
-        const uint32_t f = row_start_flags<IPT>(a, cur, kb, lane, flg, e_first, e_last);
+        uint32_t f;
+        if constexpr (MODE == kGatherSum) {
+            // The transposed product (no values) finds its row starts before issuing its
+            // gathers; the products issue their gathers first and find row starts while they
+            // are in flight (each measured the faster order for its mode).
+            if (!ok) {
+                if (lane == 0) {
+                    atomicExch(a.err, static_cast<int>(LB_ERR_BAD_MATRIX));
+                    a.carry_row[t] = -1;  // the fixup skips it
+                    a.carry_val[t] = 0.f;
+                }
+                if (has_next) {
+                    load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
+                    bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
+                }
+                cur = nxt;
+                continue;
+            }
+            load_vals<V, IPT, MODE>(a, e0, vm, pol, p);
+            f = row_start_flags<IPT>(a, cur, kb, lane, flg, e_first, e_last);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q)
+                xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) ? __ldg(a.x + col[q]) : 0.f;
+            if (has_next) {
+                load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
+                bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
+            }
+        } else {
+            // 1. This tile's gathers.
+#pragma unroll
+            for (int q = 0; q < IPT; ++q)
+                xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) ? __ldg(a.x + col[q]) : 0.f;
+
+            // 2. The next tile's indices (and the bounds of the one after) while they are in flight.
+            if (has_next) {
+                load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
+                bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
+            }
+
+            if (!ok) {
+                if (lane == 0) {
+                    atomicExch(a.err, static_cast<int>(LB_ERR_BAD_MATRIX));
+                    a.carry_row[t] = -1;  // the fixup skips it
+                    a.carry_val[t] = 0.f;
+                }
+                cur = nxt;
+                continue;
+            }
+
+            // 3. Values, and the row starts found from the row ends, while the gathers are in flight.
+            load_vals<V, IPT, MODE>(a, e0, vm, pol, p);
+            f = row_start_flags<IPT>(a, cur, kb, lane, flg, e_first, e_last);
+        }
 
         // 4. Saved gathers for the values gradient, one 32-byte store per lane when aligned.
         if (save && vm != 0u) {
