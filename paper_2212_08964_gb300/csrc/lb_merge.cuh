@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
 
             // 3. Values, and the row starts found from the row ends, while the gathers are in flight.
             load_vals<V, IPT, MODE>(a, e0, vm, pol, p);
-            f = row_start_flags<IPT>(a, cur, kb, lane, flg, e_first, e_last);
+            e_first = 0, e_last = cur.k0;
+            f = cur.r1 > cur.r0 ? row_start_flags<IPT>(a, cur, kb, lane, flg, e_first, e_last) : 0u;
         }
 
         // 4. Saved gathers for the values gradient, one 32-byte store per lane when aligned.
@@ -339,6 +340,21 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
         // 5. Products, scanned inside the lane (restarting at row starts), then across lanes.
 #pragma unroll
         for (int q = 0; q < IPT; ++q) p[q] = ((vm >> q) & 1u) ? p[q] * xv[q] : 0.f;
+        if (cur.r1 == cur.r0) {
+            // No row ends in the tile: it lies inside one row, and only its sum (the carry) is
+            // needed: the lane's products in order, then a fixed shuffle tree.
+            float sum = p[0];
+#pragma unroll
+            for (int q = 1; q < IPT; ++q) sum += p[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            if (lane == 0) {
+                a.carry_row[t] = cur.r1;
+                a.carry_val[t] = sum;
+            }
+            cur = nxt;
+            continue;
+        }
 #pragma unroll
         for (int q = 1; q < IPT; ++q)
             if (!((f >> q) & 1u)) p[q] += p[q - 1];
