@@ -194,14 +194,29 @@ __device__ __forceinline__ uint32_t row_start_flags(const MergeArgs &a, const WB
     const int nr = b.r1 - b.r0;
     e_first = 0;
     e_last = b.k0;
-    for (int j = 0; j < nr; j += 32) {
-        const bool in = j + lane < nr;
-        const int e = in ? __ldg(a.row_end + b.r0 + j + lane) : 0;
+    // One chunk of 32 row ends; row-heavy tiles (up to 248 rows) take four chunks per step,
+    // their loads issued together: one latency instead of one per chunk.
+    auto chunk = [&](int j, int e) {
         if (j == 0) e_first = e;
-        if (in && e > b.k0 && e < b.k1) flg[e - kb] = 1;
+        if (j + lane < nr && e > b.k0 && e < b.k1) flg[e - kb] = 1;
         const int src = nr - 1 - j < 31 ? nr - 1 - j : 31;
         const int el = __shfl_sync(0xffffffffu, e, src);
         if (j + 32 >= nr) e_last = el;
+    };
+    if (nr <= 32) {
+        if (nr > 0) chunk(0, lane < nr ? __ldg(a.row_end + b.r0 + lane) : 0);
+    } else {
+        for (int j0 = 0; j0 < nr; j0 += 128) {
+            int ec[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + 32 * u;
+                ec[u] = j + lane < nr ? __ldg(a.row_end + b.r0 + j + lane) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + 32 * u < nr) chunk(j0 + 32 * u, ec[u]);  // warp-uniform
+        }
     }
     __syncwarp();
     uint32_t f;
@@ -384,16 +399,29 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
         // consecutive lanes); the open row leaves as the tile's carry.
         const int nr = cur.r1 - cur.r0;
         int e_prev = cur.k0;
-        for (int j = 0; j < nr; j += 32) {
-            const bool in = j + lane < nr;
-            const int e = j == 0 ? e_first : (in ? __ldg(a.row_end + cur.r0 + j + lane) : 0);
+        auto write_rows = [&](int j, int e) {
             int ep = __shfl_up_sync(0xffffffffu, e, 1);
             if (lane == 0) ep = e_prev;
             e_prev = __shfl_sync(0xffffffffu, e, 31);
-            if (in) {
+            if (j + lane < nr) {
                 float yv = 0.f;
                 if (e > ep && e > cur.k0 && e <= cur.k1) yv = vbuf[ppad(e - 1 - kb)];
                 a.y[cur.r0 + j + lane] = yv;
+            }
+        };
+        if (nr <= 32) {
+            write_rows(0, e_first);
+        } else {
+            for (int j0 = 0; j0 < nr; j0 += 128) {
+                int ec[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + 32 * u;
+                    ec[u] = j == 0 ? e_first : (j + lane < nr ? __ldg(a.row_end + cur.r0 + j + lane) : 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + 32 * u < nr) write_rows(j0 + 32 * u, ec[u]);  // warp-uniform
             }
         }
         if (lane == 0) {
