@@ -119,39 +119,54 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
 // ------------------------------------------------------------------------------------------
 // Fixup ("Fix-up" procedure of Alg. alg:work-oriented): y[r] += the carries of row r.
 //
-// Carry rows are non-decreasing in tile order, so the carries of a row form one run.  A thread
-// takes each carry; the first carry of a run of one (a row split over two tiles: most rows)
-// adds its value to y itself.  A longer run goes to the thread's warp, which finds the run's
-// end with 32-way parallel probes, sums the run with compensated per-lane sums and a fixed
-// shuffle tree, and adds the total to y once: a fixed order, so the result is deterministic,
-// and no atomics.
+// Carry rows are non-decreasing in tile order, so the carries of a row form one run.  A warp
+// takes 32 consecutive carries at a time (one coalesced load of rows and values): the runs that
+// start and end among them are summed by one segmented shuffle scan and added to y by their
+// last lane; the run that starts among them and continues past them (at most one per warp
+// step) is summed by the whole warp, which finds the run's end with galloping and 32-way probes
+// and sums it with compensated per-lane sums (eight loads in flight per lane) and a fixed
+// shuffle tree.  A run that began before the 32 carries belongs to the warp step where it
+// began.  Every sum has a fixed order, so the result is deterministic, and there are no
+// atomics.  Carry rows outside [0, m) (the -1 of a skipped malformed tile) are skipped.
 __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *carry_row, const float *carry_val,
                                                     float *y) {
     const int lane = threadIdx.x & 31;
-    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-    for (long long c0 = static_cast<long long>(blockIdx.x) * blockDim.x; c0 < G; c0 += stride) {
-        // A thread per carry: the first carry of a row with no second one (most rows) adds its
-        // value itself; longer runs go to the warp below.
-        const long long c = c0 + threadIdx.x;
-        int r = m;
-        bool head = false, single = false;
-        if (c < G) {
-            r = __ldg(carry_row + c);
-            // Unsigned test: a carry row outside [0, m) (the -1 of a skipped malformed tile, or a
-            // value that no tile wrote) is skipped whatever it is, so y is only ever written
-            // inside [0, m).
-            head = static_cast<unsigned>(r) < static_cast<unsigned>(m) && (c == 0 || __ldg(carry_row + c - 1) != r);
-            single = head && (c + 1 >= G || __ldg(carry_row + c + 1) != r);
-            if (single) y[r] += __ldg(carry_val + c);
+    const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    for (long long c0 = ((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; c0 < G;
+         c0 += warps * 32) {
+        const long long c = c0 + lane;
+        const int r = c < G ? __ldg(carry_row + c) : -1;
+        const float v = c < G ? __ldg(carry_val + c) : 0.f;
+        const bool valid = static_cast<unsigned>(r) < static_cast<unsigned>(m);
+        int prev = __shfl_up_sync(0xffffffffu, r, 1);
+        if (lane == 0) prev = c0 > 0 ? __ldg(carry_row + c0 - 1) : -1;
+        int next = __shfl_down_sync(0xffffffffu, r, 1);
+        if (lane == 31) next = c + 1 < G ? __ldg(carry_row + c + 1) : -1;
+        const bool start = lane == 0 || prev != r;  // a segment of equal rows begins here
+        const bool head = valid && prev != r;        // a run begins here (not before c0)
+        // Segmented inclusive scan of the values over segments of equal rows.
+        const uint32_t starts = __ballot_sync(0xffffffffu, start) & (0xffffffffu >> (31 - lane));
+        const int seg = 31 - __clz(starts);  // lane 0 always starts a segment
+        float s = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float u = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane - off >= seg) s += u;
         }
-        for (unsigned todo = __ballot_sync(0xffffffffu, head && !single); todo; todo &= todo - 1) {
-            const int src = __ffs(todo) - 1;
-            const long long cs = __shfl_sync(0xffffffffu, c, src);
-            const int rs = __shfl_sync(0xffffffffu, r, src);
-            // Galloping: lane l probes cs + 2^l.
+        // A run that starts and ends among these carries: its last lane adds it.
+        const int seg_head = __shfl_sync(0xffffffffu, head ? 1 : 0, seg);
+        if (valid && next != r && seg_head) y[r] += s;
+        // The run that holds lane 31 and continues past it, when it began among these carries:
+        // the whole warp sums it.
+        const int r31 = __shfl_sync(0xffffffffu, r, 31), n31 = __shfl_sync(0xffffffffu, next, 31);
+        const int seg31 = __shfl_sync(0xffffffffu, seg, 31);
+        const bool head31 = __shfl_sync(0xffffffffu, head ? 1 : 0, seg31) != 0;
+        if (static_cast<unsigned>(r31) < static_cast<unsigned>(m) && n31 == r31 && head31) {
+            const long long cs = c0 + seg31;
+            const int rs = r31;
+            // The run's end: galloping probes (lane l probes cs + 2^l), then 32-way narrowing.
             const long long probe = cs + (1ll << lane);
-            const bool in_run = probe < G && __ldg(carry_row + probe) == rs;
-            const unsigned run_mask = __ballot_sync(0xffffffffu, in_run);
+            const unsigned run_mask = __ballot_sync(0xffffffffu, probe < G && __ldg(carry_row + probe) == rs);
             const int L = __popc(run_mask);  // probes 1, 2, .., 2^(L-1) are inside the run
             long long lo = L == 0 ? cs : cs + (1ll << (L - 1));
             long long hi = cs + (1ll << L);
@@ -159,8 +174,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
             while (hi - lo > 1) {
                 const long long step = (hi - lo + 31) / 32;
                 const long long q = lo + (lane + 1) * step;
-                const bool in = q < hi && __ldg(carry_row + q) == rs;
-                const int cnt = __popc(__ballot_sync(0xffffffffu, in));
+                const int cnt = __popc(__ballot_sync(0xffffffffu, q < hi && __ldg(carry_row + q) == rs));
                 const long long new_lo = lo + cnt * step;
                 long long new_hi = new_lo + step;
                 if (new_hi > hi) new_hi = hi;
@@ -168,8 +182,6 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
                 hi = new_hi;
             }
             const long long end = hi;  // carries [cs, end) belong to row rs
-            // Eight loads in flight per lane: a row over thousands of tiles is summed in a few
-            // memory latencies instead of one per 32 carries.
             float sum = 0.f, comp = 0.f;
             long long q = cs + lane;
             for (; q + 7 * 32 < end; q += 8 * 32) {
@@ -180,10 +192,10 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
                 for (int h = 0; h < 8; ++h) kbn_add(sum, comp, u[h]);
             }
             for (; q < end; q += 32) kbn_add(sum, comp, __ldg(carry_val + q));
-            float v = sum + comp;
+            float t = sum + comp;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) y[rs] += v;
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0) y[rs] += t;
         }
     }
 }
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(int G, int m, const int *car
 cudaError_t launch_fixup(int num_tiles, int num_rows, const int *carry_row, const float *carry_val, float *y,
                          cudaStream_t stream) {
     if (num_tiles <= 0) return cudaSuccess;
-    long long blocks = (static_cast<long long>(num_tiles) + 255) / 256;  // a thread per carry
+    long long blocks = (static_cast<long long>(num_tiles) + 255) / 256;  // a warp per 32 carries
     const long long cap = static_cast<long long>(current_sm_count()) * 8;
     if (blocks > cap) blocks = cap;
     fixup_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(num_tiles, num_rows, carry_row, carry_val, y);
