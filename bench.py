@@ -125,14 +125,29 @@ def recorded_traffic(workload: str, kernel: str):
 
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 20 ms, timestamped) around the timed region.
+
+    The sampler starts before the timed region and the region begins only after its first
+    sample has arrived, so nvidia-smi's start-up does not eat the region.  `mark_start` and
+    `mark_end` bracket the timed steps; `hold(step)` keeps running the same step, untimed, for
+    `hold_s` seconds afterwards, so that a timed region shorter than a few sampling periods
+    still has clocks recorded under the same load.  The summary reports the samples inside the
+    timed region and those of the whole loaded window (region + hold) separately; `sm_mhz` and
+    `reasons` come from the region when it holds at least three samples, else from the window,
+    and `basis` says which.
+    """
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, hold_s: float = 0.3):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.hold_s = hold_s
+        self.t_start = self.t_end = self.t_hold = None
 
     def __enter__(self):
         try:
@@ -140,10 +155,32 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", str(self.PERIOD_MS)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0  # wait (bounded) for the first sample
+            while time.time() < deadline and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
+
+    def mark_start(self):
+        self.t_start = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
+
+    def hold(self, step, sync):
+        """Run `step` (untimed) for hold_s seconds under the sampler."""
+        if self.proc is None:
+            return
+        t = time.time()
+        while time.time() - t < self.hold_s:
+            for _ in range(8):
+                step()
+            sync()
+        self.t_hold = time.time()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -153,6 +190,15 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
         if self.proc is None or not self.path:
             return None
@@ -160,17 +206,35 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        half = self.PERIOD_MS / 2000.0
+
+        def pick(t0, t1):
+            if t0 is None or t1 is None:
+                return []
+            return [r for r in rows if (ts := self._stamp(r[0])) is not None and t0 - half <= ts <= t1 + half]
+
+        def stats(sel):
+            sm = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
+            smax = [float(r[3]) for r in sel if r[3].replace(".", "").isdigit()]
+            reasons = sorted({names[i] for r in sel for i in range(4) if r[6 + i].lower() == "active"})
+            return (float(np.median(sm)) if sm else None, max(smax) if smax else None, reasons, len(sel))
+
+        region = pick(self.t_start, self.t_end)
+        window = pick(self.t_start, self.t_hold if self.t_hold is not None else self.t_end)
+        basis, sel = ("timed region", region) if len(region) >= 3 else ("timed region + untimed hold of the same step",
+                                                                          window)
+        sm, smax, reasons, n = stats(sel)
+        w_sm, _, w_reasons, w_n = stats(window)
+        all_reasons = sorted(set(reasons) | set(w_reasons))
+        return {"sm_mhz": sm, "sm_max_mhz": smax, "reasons": all_reasons, "samples": len(region),
+                "window_samples": w_n, "window_sm_mhz": w_sm, "basis": basis,
+                "period_ms": self.PERIOD_MS, "hold_s": self.hold_s}
 
 
 # ------------------------------------------------------------------------------------------
@@ -358,6 +422,7 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        clocks.mark_start()
         t0.record()
         for i in range(K):
             # The same step, with events around each pass's main kernel (recorded by the library
@@ -370,6 +435,9 @@ def run_ours(args):
             lb.set_profile_events(None, None)
         t1.record()
         torch.cuda.synchronize()
+        clocks.mark_end()
+        lb.set_profile_events(None, None)
+        clocks.hold(lambda: step(v, xd, gd), torch.cuda.synchronize)
     lb.set_profile_events(None, None)
     barrier(world)
     torch.cuda.synchronize()
