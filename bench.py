@@ -870,12 +870,12 @@ def run_stencil_precision(lb, torch, dev):
 
 
 def run_spmm(lb, torch, dev, a, plan, ci, v, xd, y):
-    """SpMM C = A B on the same matrix with B of 4, 8 and 32 columns (kc <= 4 runs the
-    warp-tiled kernel, wider B the block kernel), against kc SpMV calls.  Bytes: nonzeros
-    (value + index), row offsets, B and C once each."""
+    """SpMM C = A B on the same matrix with B of 4, 8, 16 and 32 columns (kc = 4 runs the quad
+    warp kernel, 8 and 16 the wide warp kernel, 32 the block kernel), against kc SpMV calls.
+    Bytes: nonzeros (value + index), row offsets, B and C once each."""
     out = {}
     spmv_ms = _time(torch, lambda: plan.spmv(ci, v, xd, out=y), 20)
-    for kc in (4, 8, 32):
+    for kc in (4, 8, 16, 32):
         B = torch.rand(a.n, kc, device=dev) * 2 - 1
         C = torch.empty(a.m, kc, device=dev)
         ms = _time(torch, lambda: plan.spmm(ci, v, B, out=C), 10)

@@ -742,10 +742,12 @@ lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb
         return LB_ERR_INVALID_ARG;
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
-    // kc <= 4: the warp-tiled kernel over 248-item warp tiles (the plan's own when they have
-    // that size, else a partition of its own, made on the first call that needs it).  Wider
-    // B: the block kernel over the plan's block tiles.
-    const bool warp = kc <= 4;
+    // B of 8 or 16 columns, 32-byte aligned: the wide warp-tiled kernel (8 columns of B's row
+    // per gather); kc <= 4: the warp-tiled kernel.  Both run over 248-item warp tiles (the
+    // plan's own when they have that size, else a partition of its own, made on the first call
+    // that needs it).  Other B: the block kernel over the plan's block tiles.
+    const bool wide = spmm_wide_ok(kc, B, C);
+    const bool warp = wide || kc <= 4;
     const int *tr = p->tile_row, *tn = p->tile_nz;
     int G = p->G;
     if (warp) {
@@ -786,6 +788,9 @@ lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb
         p->mm_cols = cols;
         p->mm_carry_tiles = tiles;
     }
+    if (wide)
+        return from_cuda(launch_spmm_wide(vdt, G, p->m, p->n, p->nnz, kc, tr, tn, p->ro + 1, col_idx, values, B, C,
+                                          p->mm_carry_row, p->mm_carry_val, err, stream));
     if (warp)
         return from_cuda(launch_spmm_warp(vdt, G, p->m, p->n, p->nnz, kc, tr, tn, p->ro + 1, col_idx, values, B, C,
                                           p->mm_carry_row, p->mm_carry_val, err, stream));

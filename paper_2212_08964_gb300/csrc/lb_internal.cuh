@@ -187,10 +187,16 @@ cudaError_t launch_tile_matrix(int num_tiles, const int *tile_nz, int count, con
                                int *tile_mat, cudaStream_t stream);
 
 // SpMM C = A B (B dense n x kc row-major, C m x kc), then the fixup of the carries
-// (carry_row[G], carry_val[G * kc]).  kc <= 4: over warp tiles of spmm_warp_tile_items() items
-// (a tile that fails the tile check records LB_ERR_BAD_MATRIX in err).  Otherwise: over block
-// tiles of at most 2048 items.
+// (carry_row[G], carry_val[G * kc]).  The wide and warp kernels run over warp tiles of
+// spmm_warp_tile_items() items (a tile that fails the tile check records LB_ERR_BAD_MATRIX in
+// err): the wide kernel where spmm_wide_ok holds (kc = 8 or 16, B, C and the carries 32-byte
+// aligned), the warp kernel for kc <= 4.  Otherwise: the block kernel over block tiles of at
+// most 2048 items.
 int spmm_warp_tile_items();
+bool spmm_wide_ok(int kc, const float *B, const float *C);
+cudaError_t launch_spmm_wide(lb_dtype vdt, int G, int m, int n, int nnz, int kc, const int *tile_row,
+                             const int *tile_nz, const int *row_end, const int *ci, const void *values, const float *B,
+                             float *C, int *carry_row, float *carry_val, int *err, cudaStream_t st);
 cudaError_t launch_spmm_warp(lb_dtype vdt, int G, int m, int n, int nnz, int kc, const int *tile_row,
                              const int *tile_nz, const int *row_end, const int *ci, const void *values, const float *B,
                              float *C, int *carry_row, float *carry_val, int *err, cudaStream_t st);

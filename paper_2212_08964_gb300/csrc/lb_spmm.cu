@@ -279,6 +279,284 @@ __global__ void __launch_bounds__(256, 2) spmm_warp_kernel(const SpmmArgs s) {
     }
 }
 
+// kc = 8 or 16 with B, C and the carries 32-byte aligned: the warp-tiled kernel with B's row
+// gathered 8 columns at a time, one 256-bit load per slot (one request per nonzero and chunk,
+// as in SpMV).  Per chunk, each lane walks its 8 slots once with a running sum per column: a
+// row start (a slot where row ends were counted) closes the lane's first segment (its head)
+// or a finished row, which the lane writes at once; the running sum left at the end (the
+// lane's tail, or its whole sum when no row starts in it) goes into a segmented shuffle scan
+// across lanes, whose carry-in completes the head row and the tile's open row.  The row
+// structure (counts per slot, row starts, the slots holding rows' last nonzeros) is worked
+// out once per tile and reused by every chunk.  Wider B stays on the block kernel, whose
+// threads gather a whole 128-byte row of B in one instruction: chunks gathered apart fetch
+// the same DRAM line again once B no longer fits in L2.
+constexpr int kWideCols = 8;
+
+__device__ __forceinline__ void gather_b8(const float *p, float (&r)[kWideCols]) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(p));
+}
+
+__device__ __forceinline__ void store_c8(float *p, const float (&v)[kWideCols]) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
+// 128 threads per CTA; the 8 slots' gathers hold 64 registers, so 3 CTAs (12 warps, up to 170
+// registers) per SM.
+constexpr int kWideThreads = 128;
+
+template <typename V>
+__global__ void __launch_bounds__(kWideThreads, 3) spmm_wide_kernel(const SpmmArgs s) {
+    constexpr int W = kWideCols;
+    const MergeArgs &a = s.t;
+    extern __shared__ __align__(16) int smem_cnt[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    int *cnt = smem_cnt + wib * 32 * kIpt;  // row ends per slot of the current tile
+    const int G = a.num_tiles;
+    const int nw = static_cast<int>(gridDim.x) * wpc;
+    int t = static_cast<int>(blockIdx.x) * wpc + wib;
+    if (t >= G) return;
+    *reinterpret_cast<int4 *>(cnt + kIpt * lane) = make_int4(0, 0, 0, 0);
+    *reinterpret_cast<int4 *>(cnt + kIpt * lane + 4) = make_int4(0, 0, 0, 0);
+    __syncwarp();
+    const uint64_t pol = policy_evict_first();
+    const int iph = static_cast<int>((reinterpret_cast<uintptr_t>(a.idx) >> 2) & 7);
+    const int kc = s.kc;
+    const int nch = kc / W;
+
+    auto tile_ok = [&](const WBounds &b) {
+        return b.r0 >= 0 && b.r0 <= b.r1 && b.r1 <= a.num_rows && b.k0 >= 0 && b.k0 <= b.k1 &&
+               b.k1 <= a.num_atoms && (b.r1 - b.r0) + (b.k1 - b.k0) <= 32 * kIpt - 8;
+    };
+    auto load_cols = [&](const WBounds &b, bool ok, int (&col)[kIpt]) {
+#pragma unroll
+        for (int q = 0; q < kIpt; ++q) col[q] = 0;
+        if (!ok) return;
+        const int e0 = b.k0 - ((iph + b.k0) & 7) + kIpt * lane;
+        if (e0 >= b.k1 || e0 + kIpt <= b.k0) return;
+        if (e0 >= 0 && e0 + kIpt <= a.num_atoms) {
+            uint32_t r[8];
+            ld_stream8(a.idx + e0, pol, r);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) col[q] = static_cast<int>(r[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q)
+                if (e0 + q >= b.k0 && e0 + q < b.k1) col[q] = __ldg(a.idx + e0 + q);
+        }
+    };
+
+    WBounds cur = bounds_bcast<kPlain>(bounds_word<kPlain>(a, t, lane));
+    int col[kIpt];
+    load_cols(cur, tile_ok(cur), col);
+    int bw_next = t + nw < G ? bounds_word<kPlain>(a, t + nw, lane) : 0;
+
+    for (; t < G; t += nw) {
+        const bool ok = tile_ok(cur);
+        const WBounds nxt = bounds_bcast<kPlain>(bw_next);
+        const bool has_next = t + nw < G;
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(a.err, static_cast<int>(LB_ERR_BAD_MATRIX));
+                a.carry_row[t] = -1;  // the fixup skips it
+            }
+            if (has_next) {
+                load_cols(nxt, tile_ok(nxt), col);
+                bw_next = t + 2 * nw < G ? bounds_word<kPlain>(a, t + 2 * nw, lane) : 0;
+            }
+            cur = nxt;
+            continue;
+        }
+        const int kb = cur.k0 - ((iph + cur.k0) & 7);
+        const int e0 = kb + kIpt * lane;
+        const uint32_t vm = slot_mask<kIpt>(e0, cur.k0, cur.k1);
+        uint32_t gm = 0u;  // slots whose gather is in range
+#pragma unroll
+        for (int q = 0; q < kIpt; ++q)
+            if (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) gm |= 1u << q;
+
+        // 1. The first chunk's gathers.
+        float b[kIpt][W];
+#pragma unroll
+        for (int q = 0; q < kIpt; ++q) {
+            if ((gm >> q) & 1u) {
+                gather_b8(s.B + static_cast<long long>(col[q]) * kc, b[q]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) b[q][j] = 0.f;
+            }
+        }
+
+        // 2. While they are in flight: the next tile's indices (kept apart while this tile
+        // still gathers further chunks), the values and the row structure.
+        int col_next[kIpt];
+        if (has_next) {
+            load_cols(nxt, tile_ok(nxt), col_next);
+            bw_next = t + 2 * nw < G ? bounds_word<kPlain>(a, t + 2 * nw, lane) : 0;
+        }
+        float vv[kIpt];
+        load_vals<V, kIpt, kPlain>(a, e0, vm, pol, vv);
+#pragma unroll
+        for (int q = 0; q < kIpt; ++q)
+            if (!((vm >> q) & 1u)) vv[q] = 0.f;  // slots outside the tile add nothing
+        const int nr = cur.r1 - cur.r0;
+        int e_last = cur.k0;  // end of the tile's last complete row (k0 if none)
+        for (int j = 0; j < nr; j += 32) {
+            const bool in = j + lane < nr;
+            const int e = in ? __ldg(a.row_end + cur.r0 + j + lane) : 0;
+            if (in && e >= cur.k0 && e < cur.k1) atomicAdd(cnt + (e - kb), 1);
+            if (j + 32 >= nr) e_last = __shfl_sync(0xffffffffu, e, (nr - 1) & 31);
+        }
+        __syncwarp();
+        int c[kIpt];
+        {
+            const int4 c0 = *reinterpret_cast<const int4 *>(cnt + kIpt * lane);
+            const int4 c1 = *reinterpret_cast<const int4 *>(cnt + kIpt * lane + 4);
+            c[0] = c0.x, c[1] = c0.y, c[2] = c0.z, c[3] = c0.w, c[4] = c1.x, c[5] = c1.y, c[6] = c1.z, c[7] = c1.w;
+        }
+        __syncwarp();
+        *reinterpret_cast<int4 *>(cnt + kIpt * lane) = make_int4(0, 0, 0, 0);
+        *reinterpret_cast<int4 *>(cnt + kIpt * lane + 4) = make_int4(0, 0, 0, 0);
+        uint32_t f = 0u, last = 0u, cpk0 = 0u, cpk1 = 0u;  // counts packed a byte per slot (<= 248)
+        const int c_next = __shfl_down_sync(0xffffffffu, c[0], 1);
+        int tot = 0;
+#pragma unroll
+        for (int q = 0; q < kIpt; ++q) {
+            tot += c[q];
+            if (c[q] > 0) f |= 1u << q;
+            if (q < 4)
+                cpk0 |= static_cast<uint32_t>(c[q]) << (8 * q);
+            else
+                cpk1 |= static_cast<uint32_t>(c[q]) << (8 * (q - 4));
+            const int cn = q + 1 < kIpt ? c[q + 1] : (lane < 31 ? c_next : 0);
+            const int k = e0 + q;
+            // Slot q holds a row's last nonzero: a row ends right after it inside the tile, or
+            // it is the tile's last nonzero and the tile's last complete row ends there.
+            if (((vm >> q) & 1u) && ((k + 1 < cur.k1 && cn > 0) || (k + 1 == cur.k1 && e_last == cur.k1)))
+                last |= 1u << q;
+        }
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
+        }
+        const int row_base = cur.r0 + incl - tot;  // rows ended before this lane's first slot
+        const uint32_t starts = __ballot_sync(0xffffffffu, f != 0u) & (0xffffffffu >> (31 - lane));
+        const int seg = starts ? 31 - __clz(starts) : 0;
+        const bool open_here = cur.k1 > e_last && cur.k1 - 1 >= e0 && cur.k1 - 1 < e0 + kIpt;
+        const int m = a.num_rows;
+
+#pragma unroll 1
+        for (int ch = 0; ch < nch; ++ch) {
+            if (ch > 0) {
+#pragma unroll
+                for (int q = 0; q < kIpt; ++q) {
+                    if ((gm >> q) & 1u) {
+                        gather_b8(s.B + static_cast<long long>(col[q]) * kc + ch * W, b[q]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < W; ++j) b[q][j] = 0.f;
+                    }
+                }
+            }
+            // 3. The lane's slots in order, with a running sum per column.
+            float acc[W], head[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) acc[j] = 0.f, head[j] = 0.f;
+            bool started = false;
+            int row = row_base, row_h = -1;
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q) {
+                if ((f >> q) & 1u) {
+                    if (!started) {
+#pragma unroll
+                        for (int j = 0; j < W; ++j) head[j] = acc[j];
+                    }
+                    started = true;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) acc[j] = 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j) acc[j] = fmaf(vv[q], b[q][j], acc[j]);
+                row += static_cast<int>(((q < 4 ? cpk0 : cpk1) >> (8 * (q & 3))) & 0xffu);
+                if ((last >> q) & 1u) {
+                    if (started) {
+                        if (static_cast<unsigned>(row) < static_cast<unsigned>(m))
+                            store_c8(s.C + static_cast<long long>(row) * kc + ch * W, acc);
+                    } else {
+                        row_h = row;
+                    }
+                }
+            }
+            if (!started) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) head[j] = acc[j];
+            }
+            // 4. Across lanes: lane L's running sums join those of the lanes back to the last
+            // one holding a row start (seg), whose tail begins the segment.
+            float v[W], cin[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) v[j] = acc[j];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const float vu = __shfl_up_sync(0xffffffffu, v[j], off);
+                    if (lane - off >= seg) v[j] += vu;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                cin[j] = __shfl_up_sync(0xffffffffu, v[j], 1);
+                if (lane == 0) cin[j] = 0.f;
+            }
+            if (row_h >= 0 && row_h < m) {
+                float o[W];
+#pragma unroll
+                for (int j = 0; j < W; ++j) o[j] = cin[j] + head[j];
+                store_c8(s.C + static_cast<long long>(row_h) * kc + ch * W, o);
+            }
+            if (open_here) {  // the open row's sum in this tile: its tail here, or all of it with the carry-in
+                float o[W];
+#pragma unroll
+                for (int j = 0; j < W; ++j) o[j] = started ? acc[j] : cin[j] + acc[j];
+                store_c8(s.carry_val + static_cast<long long>(t) * kc + ch * W, o);
+            }
+        }
+
+        // 5. Rows whose part inside the tile is empty, and an open row without nonzeros here.
+        int e_prev = cur.k0;
+        for (int j = 0; j < nr; j += 32) {
+            const bool in = j + lane < nr;
+            const int e = in ? __ldg(a.row_end + cur.r0 + j + lane) : 0;
+            int sp = __shfl_up_sync(0xffffffffu, e, 1);
+            if (lane == 0) sp = e_prev;
+            e_prev = __shfl_sync(0xffffffffu, e, 31);
+            if (in && e <= sp) {
+                float z[W];
+#pragma unroll
+                for (int j2 = 0; j2 < W; ++j2) z[j2] = 0.f;
+                for (int cc = 0; cc < kc; cc += W) store_c8(s.C + static_cast<long long>(cur.r0 + j + lane) * kc + cc, z);
+            }
+        }
+        if (cur.k1 <= e_last)
+            for (int cc = lane; cc < kc; cc += 32) s.carry_val[static_cast<long long>(t) * kc + cc] = 0.f;
+        if (lane == 0) a.carry_row[t] = cur.r1;
+        if (has_next) {
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q) col[q] = col_next[q];
+        }
+        __syncwarp();  // the counts are cleared for the next tile
+        cur = nxt;
+    }
+}
+
 // NQ column quads per pass (a power of two, <= THREADS); NG = THREADS / NQ nonzero ranges.
 template <typename V, int THREADS, int TMAX, bool VEC>
 __global__ void __launch_bounds__(THREADS) spmm_block_kernel(int G, int m, int n, int kc, int nq, const int *__restrict__ tile_row,
@@ -604,6 +882,65 @@ cudaError_t launch_spmm_warp(lb_dtype vdt, int G, int m, int n, int nnz, int kc,
             return vec ? launch_spmm_warp_t<__nv_bfloat16, true>(s, st) : launch_spmm_warp_t<__nv_bfloat16, false>(s, st);
         case LB_F16:
             return vec ? launch_spmm_warp_t<__half, true>(s, st) : launch_spmm_warp_t<__half, false>(s, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename V>
+static cudaError_t launch_spmm_wide_t(const SpmmArgs &s, cudaStream_t st) {
+    auto kern = spmm_wide_kernel<V>;
+    constexpr int threads = kWideThreads;
+    const size_t smem = static_cast<size_t>(threads / 32) * 32 * kIpt * sizeof(int);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    long long grid = static_cast<long long>(per_sm > 0 ? per_sm : 1) * current_sm_count();
+    const long long need = (static_cast<long long>(s.t.num_tiles) + threads / 32 - 1) / (threads / 32);
+    if (grid > need) grid = need;
+    kern<<<static_cast<int>(grid), threads, smem, st>>>(s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    long long fb = (static_cast<long long>(s.t.num_tiles) + 7) / 8;
+    const long long cap = static_cast<long long>(current_sm_count()) * 8;
+    if (fb > cap) fb = cap;
+    spmm_fixup_kernel<<<static_cast<int>(fb), 256, 0, st>>>(s.t.num_tiles, s.t.num_rows, s.kc, s.t.carry_row,
+                                                           s.carry_val, s.C);
+    return cudaGetLastError();
+}
+
+bool spmm_wide_ok(int kc, const float *B, const float *C) {
+    return (kc == 8 || kc == 16) && (reinterpret_cast<uintptr_t>(B) & 31u) == 0 &&
+           (reinterpret_cast<uintptr_t>(C) & 31u) == 0;
+}
+
+cudaError_t launch_spmm_wide(lb_dtype vdt, int G, int m, int n, int nnz, int kc, const int *tile_row,
+                             const int *tile_nz, const int *row_end, const int *ci, const void *values, const float *B,
+                             float *C, int *carry_row, float *carry_val, int *err, cudaStream_t st) {
+    if (G <= 0) return cudaSuccess;
+    if (!spmm_wide_ok(kc, B, C) || (reinterpret_cast<uintptr_t>(carry_val) & 31u) != 0) return cudaErrorInvalidValue;
+    SpmmArgs s{};
+    s.t.num_tiles = G;
+    s.t.num_rows = m;
+    s.t.num_atoms = nnz;
+    s.t.tile_row = tile_row;
+    s.t.tile_nz = tile_nz;
+    s.t.row_end = row_end;
+    s.t.idx = ci;
+    s.t.val = values;
+    s.t.x_len = n;
+    s.t.carry_row = carry_row;
+    s.t.err = err;
+    set_merge_alignment(s.t, vdt == LB_F32 ? 4 : 2);
+    s.B = B;
+    s.C = C;
+    s.kc = kc;
+    s.carry_val = carry_val;
+    switch (vdt) {
+        case LB_F32:
+            return launch_spmm_wide_t<float>(s, st);
+        case LB_BF16:
+            return launch_spmm_wide_t<__nv_bfloat16>(s, st);
+        case LB_F16:
+            return launch_spmm_wide_t<__half>(s, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -1,5 +1,6 @@
 """SpMM C = A B on the GPU against the FP64 oracle: every entry within 1e-5 * sum_k |a||b|
-(BF16/FP16 values against the oracle on the rounded values); columns of B from 1 to 160 (one
+(BF16/FP16 values against the oracle on the rounded values); columns of B from 1 to 160 (the
+wide warp kernel at 8 and 16 columns, the quad warp kernel up to 4, the block kernel with one
 and two column passes, vector and scalar paths); rows spanning many tiles, empty rows, empty
 matrices; determinism."""
 import numpy as np
@@ -36,7 +37,7 @@ def _check(C, ref, scale, tol):
 
 
 @pytest.mark.parametrize("name", ["powerlaw_4k", "long_rows", "stencil"])
-@pytest.mark.parametrize("kc", [1, 3, 4, 8, 17, 32, 64, 160])
+@pytest.mark.parametrize("kc", [1, 3, 4, 8, 12, 16, 17, 24, 32, 64, 160])
 def test_spmm_vs_oracle(lb, orc, name, kc):
     a = _cases()[name]
     ro, ci, v = to_dev(a)
@@ -78,6 +79,18 @@ def test_spmm_unaligned_and_degenerate(lb, orc):
     torch.cuda.synchronize()
     _check(C.cpu().numpy(), orc.spmm(a.row_offsets, a.col_idx, a.values, B),
            orc.spmm_absdot(a.row_offsets, a.col_idx, a.values, B), TOL32)
+    # B and C 16 bytes off a 32-byte boundary: kc = 8 leaves the wide kernel for the block
+    # kernel, kc = 4 keeps the quad warp kernel's vector path; 4 bytes off, kc = 4 takes its
+    # scalar path.
+    for kc2, off in [(8, 4), (4, 4), (4, 1)]:
+        B2 = np.random.default_rng(10 + kc2 + off).uniform(-1, 1, (a.n, kc2)).astype(np.float32)
+        Bb = torch.zeros(a.n * kc2 + off, device="cuda")
+        Bb[off:] = dev(B2.reshape(-1))
+        Cb = torch.zeros(a.m * kc2 + off, device="cuda")
+        plan.spmm(ci, v, Bb[off:].view(a.n, kc2), out=Cb[off:].view(a.m, kc2))
+        torch.cuda.synchronize()
+        _check(Cb[off:].view(a.m, kc2).cpu().numpy(), orc.spmm(a.row_offsets, a.col_idx, a.values, B2),
+               orc.spmm_absdot(a.row_offsets, a.col_idx, a.values, B2), TOL32)
     # No nonzeros: C = 0.  No columns: nothing to do.
     e = synth.CSR(5, 7, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32))
     pe = lb.Plan(dev(e.row_offsets), 7, 0, schedule="merge_path")
