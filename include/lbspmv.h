@@ -138,7 +138,8 @@ lb_status lb_spmv_static(int m, int n, int nnz, const int *row_offsets, const in
  * d_c = min(c * tile_items, m + nnz), c = 0..G with G = ceil((m + nnz) / tile_items), writes
  * tile_row[c] = #{r : r + row_offsets[r+1] < d_c} (row ends before d_c) and
  * tile_nz[c] = d_c - tile_row[c] (nonzeros before d_c).  tile_row and tile_nz are device
- * arrays of G + 1 ints.  Bit-exact; no allocation.
+ * arrays of G + 1 ints.  Bit-exact; no allocation.  A tile_items so small that G reaches
+ * 2^31 - 1 returns LB_ERR_INVALID_ARG.
  */
 lb_status lb_partition(int m, int nnz, const int *row_offsets, int tile_items, int *tile_row,
                        int *tile_nz, cudaStream_t stream);

@@ -329,6 +329,7 @@ lb_status lb_partition(int m, int nnz, const int *row_offsets, int tile_items, i
     LB_NVTX_RANGE();
     if (m < 0 || nnz < 0 || tile_items <= 0 || (m == 0 && nnz != 0)) return LB_ERR_INVALID_ARG;
     if (!row_offsets || !tile_row || !tile_nz) return LB_ERR_INVALID_ARG;
+    if ((static_cast<long long>(m) + nnz + tile_items - 1) / tile_items >= INT_MAX) return LB_ERR_INVALID_ARG;
     return from_cuda(launch_partition(m, nnz, row_offsets, tile_items, tile_row, tile_nz, stream));
 }
 

@@ -36,62 +36,71 @@ __global__ void __launch_bounds__(256) partition_kernel(int m, long long W, int 
     const int lane = threadIdx.x & 31;
     const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const long long warps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+    const unsigned Tu = static_cast<unsigned>(T);
+    const int Gi = static_cast<int>(G);  // G < 2^31 (checked on the host)
     for (long long base0 = warp * 32 * U; base0 <= m; base0 += warps * 32 * U) {
-        // Each lane loads offsets[r+1] of its row in every chunk; offsets[r] comes from the lane
-        // below (lane 0 loads it).
-        int end_offs[U], lane0_start[U];
+        // Each lane loads offsets[r+1] of its row in every chunk; lane 0 also loads offsets[r]
+        // of the step's first row, whose predecessor lies outside the step.
+        int end_offs[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long r = base0 + 32 * u + lane;
             end_offs[u] = (r < m) ? __ldg(offsets + r + 1) : 0;
-            lane0_start[u] = (lane == 0 && r > 0 && r <= m) ? __ldg(offsets + r) : 0;
         }
+        const int start0 = (lane == 0 && base0 > 0 && base0 <= m) ? __ldg(offsets + base0) : 0;
+        // Tile of the row end before the step's first row: K_{r-1} / T, or -1 before row 0.
+        int q_carry = -1;
+        if (base0 > 0) {
+            const unsigned qc = static_cast<unsigned>((base0 - 1) + static_cast<long long>(start0)) / Tu;
+            q_carry = qc < static_cast<unsigned>(Gi) ? static_cast<int>(qc) : Gi;
+        }
+        q_carry = __shfl_sync(0xffffffffu, q_carry, 0);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long base = base0 + 32 * u;
             if (base > m) break;  // warp-uniform
             const long long r = base + lane;
-            long long c_lo = 0, n_c = 0;
-            const int end_off = end_offs[u];
-            int start_off = __shfl_up_sync(0xffffffffu, end_off, 1);
-            if (lane == 0) start_off = lane0_start[u];
-            if (r <= m) {
-                // Merge positions fit 32 bits (m + nnz < 2^32): 32-bit division, not 64-bit.
-                const long long k_prev = (r == 0) ? -1 : (r - 1) + static_cast<long long>(start_off);
-                const long long k_cur = (r == m) ? W : r + static_cast<long long>(end_off);
-                const unsigned Tu = static_cast<unsigned>(T);
-                c_lo = k_prev + 1 > 0 ? (static_cast<unsigned>(k_prev) + Tu) / Tu : 0;
-                long long c_hi = (r == m) ? G : static_cast<unsigned>(k_cur) / Tu;
-                if (c_hi > G) c_hi = G;  // only malformed offsets get here; keep writes in [0, G]
-                n_c = c_hi >= c_lo ? c_hi - c_lo + 1 : 0;
+            // Boundaries c with K_{r-1} < c T <= K_r (and c = G at row m) are those with
+            // q(r-1) < c <= q(r), where q(r) = K_r / T (rounded down) and K_r = r + offsets[r+1]
+            // fits 32 bits (m + nnz < 2^32); q(r) = G from row m on.  One division per row: q(r-1)
+            // comes from the lane below.  Tile indices and counts are below G < 2^31.
+            int q_cur = Gi;
+            if (r < m) {
+                const unsigned qc = static_cast<unsigned>(r + static_cast<long long>(end_offs[u])) / Tu;
+                q_cur = qc < static_cast<unsigned>(Gi) ? static_cast<int>(qc) : Gi;  // malformed offsets: keep writes in [0, G]
             }
+            int q_prev = __shfl_up_sync(0xffffffffu, q_cur, 1);
+            if (lane == 0) q_prev = q_carry;
+            q_carry = __shfl_sync(0xffffffffu, q_cur, 31);
+            const int c_lo = q_prev + 1;
+            const int n_c = r <= m && q_cur > q_prev ? q_cur - q_prev : 0;
             if (__ballot_sync(0xffffffffu, n_c > 0) == 0u) continue;  // no boundary in these 32 rows (most)
             // Exclusive prefix of the per-lane boundary counts.
-            long long incl = n_c;
+            int incl = n_c;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const long long t = __shfl_up_sync(0xffffffffu, incl, off);
+                const int t = __shfl_up_sync(0xffffffffu, incl, off);
                 if (lane >= off) incl += t;
             }
-            const long long total = __shfl_sync(0xffffffffu, incl, 31);
-            const long long excl = incl - n_c;
-            for (long long q0 = 0; q0 < total; q0 += 32) {  // warp-uniform trip count
-                const long long q = q0 + lane;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int excl = incl - n_c;
+            for (int q0 = 0; q0 < total; q0 += 32) {  // warp-uniform trip count
+                const int q = q0 + lane;
                 // Owner: the last lane whose exclusive prefix is <= q.
                 int lo = 0, hi = 31;
 #pragma unroll
                 for (int step = 0; step < 5; ++step) {
                     const int mid = (lo + hi + 1) >> 1;
-                    const long long e_mid = __shfl_sync(0xffffffffu, excl, mid);
+                    const int e_mid = __shfl_sync(0xffffffffu, excl, mid);
                     if (e_mid <= q)
                         lo = mid;
                     else
                         hi = mid - 1;
                 }
-                const long long e_own = __shfl_sync(0xffffffffu, excl, lo);
-                const long long c_own = __shfl_sync(0xffffffffu, c_lo, lo);
+                const int e_own = __shfl_sync(0xffffffffu, excl, lo);
+                const int c_own = __shfl_sync(0xffffffffu, c_lo, lo);
                 if (q >= total) continue;
-                const long long c = c_own + (q - e_own);
+                const long long c = static_cast<long long>(c_own) + (q - e_own);
                 const long long row = base + lo;
                 const long long d = c * T < W ? c * T : W;
                 if (!LB_IN_RANGE(c, G + 1)) continue;
@@ -106,8 +115,10 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
                              cudaStream_t stream) {
     const long long W = static_cast<long long>(m) + nnz;
     const long long G = (W + tile_items - 1) / tile_items;
-    // A warp per four 32-row chunks (their loads in flight together), grid-strided beyond one
-    // wave of 16 blocks per SM.
+    if (G >= INT_MAX) return cudaErrorInvalidValue;  // the kernel counts tiles in 32 bits
+    // A warp per four 32-row chunks (their loads in flight together), grid-strided beyond
+    // 16 blocks per SM (several waves: a warp held up by a row spanning many tiles leaves the
+    // SM to the next wave's blocks).
     long long blocks = (static_cast<long long>(m) + 1 + 1023) / 1024;
     const long long cap = static_cast<long long>(current_sm_count()) * 16;
     if (blocks > cap) blocks = cap;

@@ -59,6 +59,10 @@ def test_host_side_argument_rejection(lib):
     assert lib.lb_spmv(4, 4, 4, None, None, None, 7, None, None, None) == -1
     assert lib.lb_spmv(0, 0, 0, None, None, None, 0, None, None, None) == 0  # m == 0: no-op
     assert lib.lb_partition(4, 6, None, 0, None, None, None) == -1
+    # Tiles of one item over 2^31 work items: a tile count beyond 32 bits, refused on the host
+    # (the pointers are never dereferenced).
+    fake = ctypes.c_void_p(256)
+    assert lib.lb_partition(1 << 30, (1 << 31) - 1, fake, 1, fake, fake, None) == -1
     out = P()
     assert lib.lb_plan_create(4, 4, 4, None, 0, None, None, ctypes.byref(out)) == -1  # null offsets
     assert lib.lb_plan_create(4, 4, 4, ctypes.c_void_p(16), 99, None, None, ctypes.byref(out)) == -1  # bad schedule
