@@ -59,6 +59,8 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     p.add_argument("--no-secondary", action="store_true",
                    help="skip the secondary lines (BF16/FP16 step, batched vs per-matrix)")
+    p.add_argument("--spmm-only", action="store_true",
+                   help="time only SpMM on the workload and print its line (small cases for profiler captures)")
     return p.parse_args(argv)
 
 
@@ -396,6 +398,11 @@ def run_ours(args):
     dv = torch.empty(a.nnz, device=dev)
     xg = torch.empty(a.nnz, device=dev)
     plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    if args.spmm_only:
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "scale": args.scale, "nnz": int(a.nnz),
+                              "spmm": run_spmm(lb, torch, dev, a, plan, ci, v, xd, y)}))
+        return 0
     plan.build_transpose(ci)
     info = plan.info()
     torch.cuda.synchronize()

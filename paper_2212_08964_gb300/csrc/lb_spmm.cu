@@ -304,12 +304,17 @@ __device__ __forceinline__ void store_c8(float *p, const float (&v)[kWideCols]) 
                  : "memory");
 }
 
-// 128 threads per CTA; the 8 slots' gathers hold 64 registers, so 3 CTAs (12 warps, up to 170
-// registers) per SM.
+// 128 threads per CTA.  A lane's 8 slots gather in two groups of 4 (32 registers in flight):
+// the second group's gathers go out when the first group's products are summed.  That fits
+// 128 registers, 4 CTAs (16 warps) per SM; all 8 slots in flight at once take 167 registers
+// and 12 warps, measured 10% slower when B fits in L2 (and the same when it does not), and 4
+// groups of 2 slower at every size.
 constexpr int kWideThreads = 128;
+constexpr int kWideMinBlocks = 4;
+constexpr int kWideGroups = 2;
 
 template <typename V>
-__global__ void __launch_bounds__(kWideThreads, 3) spmm_wide_kernel(const SpmmArgs s) {
+__global__ void __launch_bounds__(kWideThreads, kWideMinBlocks) spmm_wide_kernel(const SpmmArgs s) {
     constexpr int W = kWideCols;
     const MergeArgs &a = s.t;
     extern __shared__ __align__(16) int smem_cnt[];
@@ -380,17 +385,22 @@ __global__ void __launch_bounds__(kWideThreads, 3) spmm_wide_kernel(const SpmmAr
         for (int q = 0; q < kIpt; ++q)
             if (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) gm |= 1u << q;
 
-        // 1. The first chunk's gathers.
-        float b[kIpt][W];
+        // 1. The first chunk's gathers (of its first slot group).
+        constexpr int GS = kIpt / kWideGroups;
+        float b[GS][W];
+        auto gather_group = [&](int g, int ch) {
 #pragma unroll
-        for (int q = 0; q < kIpt; ++q) {
-            if ((gm >> q) & 1u) {
-                gather_b8(s.B + static_cast<long long>(col[q]) * kc, b[q]);
-            } else {
+            for (int i = 0; i < GS; ++i) {
+                const int q = g * GS + i;
+                if ((gm >> q) & 1u) {
+                    gather_b8(s.B + static_cast<long long>(col[q]) * kc + ch * W, b[i]);
+                } else {
 #pragma unroll
-                for (int j = 0; j < W; ++j) b[q][j] = 0.f;
+                    for (int j = 0; j < W; ++j) b[i][j] = 0.f;
+                }
             }
-        }
+        };
+        gather_group(0, 0);
 
         // 2. While they are in flight: the next tile's indices (kept apart while this tile
         // still gathers further chunks), the values and the row structure.
@@ -454,17 +464,6 @@ __global__ void __launch_bounds__(kWideThreads, 3) spmm_wide_kernel(const SpmmAr
 
 #pragma unroll 1
         for (int ch = 0; ch < nch; ++ch) {
-            if (ch > 0) {
-#pragma unroll
-                for (int q = 0; q < kIpt; ++q) {
-                    if ((gm >> q) & 1u) {
-                        gather_b8(s.B + static_cast<long long>(col[q]) * kc + ch * W, b[q]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < W; ++j) b[q][j] = 0.f;
-                    }
-                }
-            }
             // 3. The lane's slots in order, with a running sum per column.
             float acc[W], head[W];
 #pragma unroll
@@ -473,6 +472,8 @@ __global__ void __launch_bounds__(kWideThreads, 3) spmm_wide_kernel(const SpmmAr
             int row = row_base, row_h = -1;
 #pragma unroll
             for (int q = 0; q < kIpt; ++q) {
+                if (q % GS == 0 && (ch > 0 || q > 0)) gather_group(q / GS, ch);
+                const float *bq = b[q % GS];
                 if ((f >> q) & 1u) {
                     if (!started) {
 #pragma unroll
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kWideThreads, 3) spmm_wide_kernel(const SpmmAr
                     for (int j = 0; j < W; ++j) acc[j] = 0.f;
                 }
 #pragma unroll
-                for (int j = 0; j < W; ++j) acc[j] = fmaf(vv[q], b[q][j], acc[j]);
+                for (int j = 0; j < W; ++j) acc[j] = fmaf(vv[q], bq[j], acc[j]);
                 row += static_cast<int>(((q < 4 ? cpk0 : cpk1) >> (8 * (q & 3))) & 0xffu);
                 if ((last >> q) & 1u) {
                     if (started) {
