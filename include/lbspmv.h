@@ -283,13 +283,17 @@ lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const v
 
 /*
  * SpMM: C = A B with B dense (n x kc, row-major, FP32) and C (m x kc, row-major, FP32,
- * overwritten), over the plan's merge-path partition: the dissertation's SpMV with a loop over
- * the columns of B (Ch.4 Sec. "Application Space", the SpMM listing).  Each nonzero gathers a
- * row of B as 16-byte vectors (scalar loads when kc % 4 != 0 or B, C are not 16-byte aligned);
- * rows split across tiles are completed by a fixup of kc-wide carries in tile order, so C is
- * deterministic.  Plans whose tiles exceed 2048 work items give LB_ERR_UNSUPPORTED.  The
- * first call (and any call with more columns than before) allocates the plan's carry buffer
- * (G * (kc + 1) * 4 bytes); later calls allocate nothing.
+ * overwritten), over merge-path tiles of the plan's matrix: the dissertation's SpMV with a loop
+ * over the columns of B (Ch.4 Sec. "Application Space", the SpMM listing).  kc = 8 or 16 with B
+ * and C 32-byte aligned: 248-item warp tiles, each nonzero gathering 8 columns of B's row in
+ * one 32-byte load per chunk; kc <= 4: the same warp tiles with 16-byte (or scalar) gathers;
+ * other kc: the plan's block tiles, 16-byte vectors of B per thread (scalar loads when
+ * kc % 4 != 0 or B, C are not 16-byte aligned).  Rows split across tiles are completed by a
+ * fixup of kc-wide carries in tile order, so C is deterministic.  On the block tiles, plans
+ * whose tiles exceed 2048 work items give LB_ERR_UNSUPPORTED.  The first call (and any call
+ * with more columns or tiles than before) allocates the plan's carry buffer (G * (kc + 1) * 4
+ * bytes), and the first warp-tile call on a plan whose own tiles are not 248 items allocates
+ * and builds a partition of its own; later calls allocate nothing.
  */
 lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, int kc,
                           const float *B, float *C, cudaStream_t stream);
