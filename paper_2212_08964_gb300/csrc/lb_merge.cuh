@@ -97,14 +97,18 @@ __device__ __forceinline__ int batched_col_base(const MergeArgs &a, int m0, int 
     return __ldg(a.mat_col_base + lo);
 }
 
-// This lane's gather indices for one tile (with the matrix's column base when batched).
-// Lanes whose slots all lie outside the tile load nothing; slots outside the tile may hold
-// neighbouring indices, which are never gathered.
+// This lane's gather indices for one tile.  Batched: a tile inside one matrix returns that
+// matrix's column base in cb, added only when the gathers are issued (adding it here would
+// wait for the index load at once, instead of while the current tile is worked on); a tile
+// spanning matrices adds each slot's base to its index and returns cb = 0.  Lanes whose slots
+// all lie outside the tile load nothing; slots outside the tile may hold neighbouring indices,
+// which are never gathered.
 template <int IPT, int MODE>
 __device__ __forceinline__ void load_idx(const MergeArgs &a, const WBounds &b, bool ok, int iph, int lane,
-                                         uint64_t pol, int (&col)[IPT]) {
+                                         uint64_t pol, int (&col)[IPT], int &cb) {
 #pragma unroll
     for (int q = 0; q < IPT; ++q) col[q] = 0;
+    cb = 0;
     if (!ok) return;
     const int lead = (iph + b.k0) & 7;
     const int e0 = b.k0 - lead + IPT * lane;
@@ -124,9 +128,7 @@ __device__ __forceinline__ void load_idx(const MergeArgs &a, const WBounds &b, b
     }
     if (MODE == kBatched) {
         if (b.m0 == b.m1) {
-            const int base = __ldg(a.mat_col_base + b.m0);
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) col[q] += base;
+            cb = __ldg(a.mat_col_base + b.m0);
         } else {
 #pragma unroll
             for (int q = 0; q < IPT; ++q)
@@ -269,8 +271,8 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
     const bool save = MODE == kPlain && a.xg != nullptr;
 
     WBounds cur = bounds_bcast<MODE>(bounds_word<MODE>(a, t, lane));
-    int col[IPT];
-    load_idx<IPT, MODE>(a, cur, wtile_ok<IPT>(a, cur), iph, lane, pol, col);
+    int col[IPT], cb;
+    load_idx<IPT, MODE>(a, cur, wtile_ok<IPT>(a, cur), iph, lane, pol, col, cb);
     int bw_next = t + nw < G ? bounds_word<MODE>(a, t + nw, lane) : 0;
 
     for (; t < G; t += nw) {
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
                     a.carry_val[t] = 0.f;
                 }
                 if (has_next) {
-                    load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
+                    load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col, cb);
                     bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
                 }
                 cur = nxt;
@@ -307,20 +309,20 @@ __global__ void __launch_bounds__(MergeLaunch<IPT>::MAX_THREADS, MergeLaunch<IPT
             f = row_start_flags<IPT>(a, cur, kb, lane, flg, e_first, e_last);
 #pragma unroll
             for (int q = 0; q < IPT; ++q)
-                xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) ? __ldg(a.x + col[q]) : 0.f;
+                xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q] + cb, a.x_len)) ? __ldg(a.x + (col[q] + cb)) : 0.f;
             if (has_next) {
-                load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
+                load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col, cb);
                 bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
             }
         } else {
             // 1. This tile's gathers.
 #pragma unroll
             for (int q = 0; q < IPT; ++q)
-                xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q], a.x_len)) ? __ldg(a.x + col[q]) : 0.f;
+                xv[q] = (((vm >> q) & 1u) && LB_IN_RANGE(col[q] + cb, a.x_len)) ? __ldg(a.x + (col[q] + cb)) : 0.f;
 
             // 2. The next tile's indices (and the bounds of the one after) while they are in flight.
             if (has_next) {
-                load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col);
+                load_idx<IPT, MODE>(a, nxt, wtile_ok<IPT>(a, nxt), iph, lane, pol, col, cb);
                 bw_next = t + 2 * nw < G ? bounds_word<MODE>(a, t + 2 * nw, lane) : 0;
             }
 
