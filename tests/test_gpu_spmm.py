@@ -54,11 +54,13 @@ def test_spmm_vs_oracle(lb, orc, name, kc):
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
-def test_spmm_half_values(lb, orc, dtype):
+@pytest.mark.parametrize("kc", [4, 8, 16, 24])
+def test_spmm_half_values(lb, orc, dtype, kc):
+    """16-bit values through every SpMM kernel: quad warp (4), wide warp (8, 16), block (24)."""
     a = _long_rows()
     ro, ci, v = to_dev(a, dtype)
     plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
-    B = np.random.default_rng(5).uniform(-1, 1, (a.n, 16)).astype(np.float32)
+    B = np.random.default_rng(5).uniform(-1, 1, (a.n, kc)).astype(np.float32)
     C = plan.spmm(ci, v, dev(B))
     torch.cuda.synchronize()
     vals = rounded(a.values, dtype)
