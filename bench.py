@@ -61,6 +61,8 @@ def parse_args(argv=None):
                    help="skip the secondary lines (BF16/FP16 step, batched vs per-matrix)")
     p.add_argument("--spmm-only", action="store_true",
                    help="time only SpMM on the workload and print its line (small cases for profiler captures)")
+    p.add_argument("--batched-only", action="store_true",
+                   help="time only the two batch classes and print their line (for profiler captures)")
     return p.parse_args(argv)
 
 
@@ -386,6 +388,10 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library is the only compute path)")
     torch.cuda.set_device(local)
     lb.ensure_loaded()
+    if args.batched_only:
+        if rank == 0:
+            print(json.dumps({"batched": run_batched(lb, torch, torch.device("cuda", local))}))
+        return 0
     a, x, g = make_inputs(args.workload, args.scale)
     dev = torch.device("cuda", local)
     ro = torch.from_numpy(a.row_offsets).to(dev)
