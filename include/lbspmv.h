@@ -69,9 +69,10 @@ typedef enum { LB_F32 = 0, LB_BF16 = 1, LB_F16 = 2 } lb_dtype;
 
 /* Launch shape of a schedule; 0 selects the default.
  *   merge-path:   (threads, items_per_thread) in {(128, 16), (256, 8), (256, 16), (384, 8),
- *                 (512, 8)}, default (256, 8).  `threads` counts the gather threads
- *                 of a CTA (scan and producer warps are added); one tile holds
- *                 threads * items_per_thread - 8 work items (rows + nonzeros);
+ *                 (512, 8)}, default (256, 8): CTAs of `threads` threads whose warps each
+ *                 work one tile at a time of 32 * items_per_thread - 8 work items (rows +
+ *                 nonzeros); the plan's block-level passes (SpMM beyond the warp kernels,
+ *                 the transpose) use tiles of threads * items_per_thread - 8 items;
  *   block-mapped: threads in {128, 256} (the group is the block);
  *   group-mapped: group_size in {4, 8, 16, 32}. */
 typedef struct {
