@@ -383,12 +383,16 @@ lb_status lb_tune_batched(int count, const int *h_m, const int *h_n, const int *
  * load-balancing schedules as in Ch.4 Sec. "Application Space" (the SSSP listing): the
  * frontier's edges are the atoms, split evenly over the threads; relaxing an edge lowers the
  * neighbour's distance with an atomic minimum and puts the neighbour on the next frontier when
- * it dropped; the host iterates until the frontier is empty.  weights: nnz non-negative FP32
- * values, or NULL for unit weights (dist = BFS level).  dist (n floats, device) receives the
- * distances (+inf when unreachable); *iterations (host) the number of frontier iterations.
- * FP32 sums: each distance is the minimum over paths of the FP32 sum along the path.
- * Allocates its workspace (about 16 bytes per vertex) and synchronizes `stream` once per
- * iteration.  Negative weights are not supported (the iteration count is capped at n + 1).
+ * it dropped; the host iterates until the frontier is empty.  With weights the frontier is
+ * split by distance (near-far, Davidson et al., IPDPS 2014): neighbours whose new distance
+ * reaches the split point are set aside and join a later frontier when the split point
+ * advances (by delta = mean weight * 8 / mean degree).  weights: nnz non-negative FP32 values,
+ * or NULL for unit weights (dist = BFS level, one level per iteration).  dist (n floats,
+ * device) receives the distances (+inf when unreachable); *iterations (host) the number of
+ * frontier iterations.  FP32 sums: each distance is the minimum over paths of the FP32 sum
+ * along the path, whatever the order of relaxation.  Allocates its workspace (about 24 bytes
+ * per vertex) and synchronizes `stream` once per iteration and once per advance of the split
+ * point.  Negative weights are not supported.
  */
 lb_status lb_sssp(int n, int nnz, const int *row_offsets, const int *col_idx, const float *weights,
                   int source, float *dist, int *iterations, cudaStream_t stream);
