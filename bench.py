@@ -413,11 +413,15 @@ def run_ours(args):
     info = plan.info()
     torch.cuda.synchronize()
 
+    # The values gradient in the values' type, as the autograd function stores it.
+    dv_of = {torch.float32: dv, torch.bfloat16: torch.empty(a.nnz, dtype=torch.bfloat16, device=dev),
+             torch.float16: torch.empty(a.nnz, dtype=torch.float16, device=dev)}
+
     def step(vals, xx, gg):
         # The training step of y = A x under autograd: forward (saving x[col] per nonzero for
         # the values gradient), then dx = A^T g and dvalues = g[row] * x[col] together.
         plan.spmv(ci, vals, xx, out=y, save_gathered=xg)
-        plan.backward(vals, gg, xg, dx=dx, dvalues=dv)
+        plan.backward(vals, gg, xg, dx=dx, dvalues=dv_of[vals.dtype])
 
     launches_per_step = 2 + 3
     fwd_b, bwd_t_b, dv_b = step_bytes(a.m, a.n, a.nnz)
@@ -745,15 +749,17 @@ def run_tuned_precision(lb, torch, a, ro, ci, v, xd, gd, y, dx, dv, xg):
         plan, shape = _tuned_plan(lb, torch, a, ro, name)
         plan.build_transpose(ci)
         vd = v.to(getattr(torch, tname))
+        dvd = dv if vd.dtype == torch.float32 else torch.empty(a.nnz, dtype=vd.dtype, device=dv.device)
 
         def step():
             plan.spmv(ci, vd, xd, out=y, save_gathered=xg)
-            plan.backward(vd, gd, xg, dx=dx, dvalues=dv)
+            plan.backward(vd, gd, xg, dx=dx, dvalues=dvd)
 
         out[name] = {"config": shape, "forward_ms": _time(torch, lambda: plan.spmv(ci, vd, xd, out=y), 20),
                      "forward_save_ms": _time(torch, lambda: plan.spmv(ci, vd, xd, out=y, save_gathered=xg), 20),
-                     "backward_ms": _time(torch, lambda: plan.backward(vd, gd, xg, dx=dx, dvalues=dv), 20),
+                     "backward_ms": _time(torch, lambda: plan.backward(vd, gd, xg, dx=dx, dvalues=dvd), 20),
                      "step_ms": _time(torch, step, 20)}
+        del dvd
         del plan
     for name in ("bf16", "f16"):
         out[f"{name}_forward_speedup_vs_f32"] = out["f32"]["forward_ms"] / out[name]["forward_ms"]

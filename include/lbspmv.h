@@ -18,7 +18,9 @@
  *     "host".  The library never frees caller memory.  Any alignment is accepted.
  *   - Indices are int32: row_offsets[m+1] (row_offsets[0] == 0, non-decreasing,
  *     row_offsets[m] == nnz), col_idx[nnz] in [0, n).  Values are FP32, BF16 or FP16
- *     (lb_dtype); x, y, g, dx and dvalues are FP32; accumulation is FP32.
+ *     (lb_dtype); x, y, g and dx are FP32; the values gradient dvalues is FP32 or, where a
+ *     call takes its type (dvdt), BF16/FP16 rounded to nearest even from the FP32 product
+ *     (the storage an autograd engine expects for 16-bit values); accumulation is FP32.
  *   - y is OVERWRITTEN: y = A x (no beta).  Empty rows give 0.  m == 0 is a no-op;
  *     nnz == 0 gives y = 0.
  *   - Work is stream-ordered on `stream` (0 = the legacy default stream).  No call
@@ -231,10 +233,11 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
 /*
  * dvalues[k] = g[row(k)] * x[col_idx[k]] (backward of y = A x with respect to the values),
  * one coalesced pass over the nonzeros; row(k) comes from the plan's merge-path partition
- * (each tile stages its row ends and searches them).  Merge-path plans only.
+ * (each tile stages its row ends and searches them).  Merge-path plans only.  dvalues: nnz
+ * elements of dvdt (LB_F32, LB_BF16 or LB_F16: the FP32 product rounded to nearest even).
  */
 lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x,
-                          float *dvalues, cudaStream_t stream);
+                          void *dvalues, lb_dtype dvdt, cudaStream_t stream);
 
 /*
  * y = A x with a merge-path plan (as lb_spmv_planned), also saving the gathered operand of
@@ -250,19 +253,22 @@ lb_status lb_spmv_planned_save(const lb_plan *p, const int *col_idx, const void 
 /*
  * dvalues[k] = g[row(k)] * x_gathered[k] with x_gathered from lb_spmv_planned_save (the same
  * values as lb_spmv_dvalues, bit for bit); row(k) from the plan's forward partition.
+ * dvalues: nnz elements of dvdt, as lb_spmv_dvalues.
  */
-lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
-                                   cudaStream_t stream);
+lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, void *dvalues,
+                                   lb_dtype dvdt, cudaStream_t stream);
 
 /*
  * Both gradients of y = A x in one go: dvalues[k] = g[row(k)] * x_gathered[k] (x_gathered from
  * lb_spmv_planned_save) is formed in the same CSR-order pass that prepares the scaled values
  * for dx = A^T g (see lb_spmv_t), so the backward is two passes over the nonzeros instead of
  * three.  Results equal lb_spmv_t's dx and lb_spmv_dvalues_gathered's dvalues bit for bit.
- * Requires lb_plan_build_transpose; dx (n floats) and dvalues (nnz floats) are overwritten.
+ * Requires lb_plan_build_transpose; dx (n floats) and dvalues (nnz elements of dvdt: LB_F32,
+ * or vdt itself for 16-bit values) are overwritten; any other dvdt is LB_ERR_INVALID_ARG.
  */
 lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
-                           const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream);
+                           const float *x_gathered, float *dx, void *dvalues, lb_dtype dvdt,
+                           cudaStream_t stream);
 
 /*
  * The backward without a CSC view, and not bit-reproducible: one streaming pass over the
@@ -276,11 +282,12 @@ lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, c
  * trade reproducibility for one pass and no CSC plan memory.
  * col_idx: nnz ints; values: nnz of vdt; g: m floats; x_gathered: nnz floats from
  * lb_spmv_planned_save (may be NULL when dvalues is NULL); dx: n floats, overwritten (zeroed,
- * then accumulated); dvalues: nnz floats or NULL.  Needs only the plan's forward partition.
+ * then accumulated); dvalues: nnz elements of dvdt (LB_F32, or vdt itself for 16-bit values)
+ * or NULL.  Needs only the plan's forward partition.
  */
 lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
-                                   const float *g, const float *x_gathered, float *dx, float *dvalues,
-                                   cudaStream_t stream);
+                                   const float *g, const float *x_gathered, float *dx, void *dvalues,
+                                   lb_dtype dvdt, cudaStream_t stream);
 
 /*
  * SpMM: C = A B with B dense (n x kc, row-major, FP32) and C (m x kc, row-major, FP32,

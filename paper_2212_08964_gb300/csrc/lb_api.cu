@@ -644,11 +644,13 @@ lb_status lb_plan_transpose(const lb_plan *p, int *col_offsets, int *row_idx, in
 // order into L2-sized buckets of CSC order (with dvalues alongside when asked), then the
 // merge-path gather-sum over the columns.
 static lb_status transposed_product(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
-                                    const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream) {
+                                    const float *x_gathered, float *dx, void *dvalues, bool dv_narrow,
+                                    cudaStream_t stream) {
     int *err = device_error_word();
     if (!err) return LB_ERR_CUDA;
     cudaError_t e = launch_csr_backward(vdt, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row, p->w_tile_nz,
-                                        p->ro + 1, g, values, p->bucket_pos, p->pv, x_gathered, dvalues, stream);
+                                        p->ro + 1, g, values, p->bucket_pos, p->pv, x_gathered, dvalues, dv_narrow,
+                                        stream);
     if (e != cudaSuccess) return from_cuda(e);
     MergeArgs a{};
     a.num_tiles = p->Gt;
@@ -679,25 +681,29 @@ lb_status lb_spmv_t(const lb_plan *p, const void *values, lb_dtype vdt, const fl
     if (!dx || (p->nnz > 0 && (!values || !g))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return from_cuda(cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream));
-    return transposed_product(p, values, vdt, g, nullptr, dx, nullptr, stream);
+    return transposed_product(p, values, vdt, g, nullptr, dx, nullptr, false, stream);
 }
 
 lb_status lb_spmv_backward(const lb_plan *p, const void *values, lb_dtype vdt, const float *g,
-                           const float *x_gathered, float *dx, float *dvalues, cudaStream_t stream) {
+                           const float *x_gathered, float *dx, void *dvalues, lb_dtype dvdt, cudaStream_t stream) {
     LB_NVTX_RANGE();
     if (!p || !p->has_t || !dtype_ok(vdt) || !dx || !dvalues) return LB_ERR_INVALID_ARG;
+    if (dvdt != LB_F32 && dvdt != vdt) return LB_ERR_INVALID_ARG;
     if (p->nnz > 0 && (!values || !g || !x_gathered)) return LB_ERR_INVALID_ARG;
+    if (!aligned(dvalues, value_bytes(dvdt))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->n == 0) return LB_OK;
     if (p->nnz == 0) return from_cuda(cudaMemsetAsync(dx, 0, static_cast<size_t>(p->n) * sizeof(float), stream));
-    return transposed_product(p, values, vdt, g, x_gathered, dx, dvalues, stream);
+    return transposed_product(p, values, vdt, g, x_gathered, dx, dvalues, dvdt != LB_F32, stream);
 }
 
 lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt,
-                                   const float *g, const float *x_gathered, float *dx, float *dvalues,
+                                   const float *g, const float *x_gathered, float *dx, void *dvalues, lb_dtype dvdt,
                                    cudaStream_t stream) {
     LB_NVTX_RANGE();
     if (!p || !dtype_ok(vdt) || !dx) return LB_ERR_INVALID_ARG;
+    if (dvdt != LB_F32 && dvdt != vdt) return LB_ERR_INVALID_ARG;
+    if (dvalues && !aligned(dvalues, value_bytes(dvdt))) return LB_ERR_INVALID_ARG;
     if (p->nnz > 0 && (!col_idx || !values || !g || (dvalues && !x_gathered))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
     if (p->n == 0) return LB_OK;
@@ -705,29 +711,31 @@ lb_status lb_spmv_backward_scatter(const lb_plan *p, const int *col_idx, const v
     if (e != cudaSuccess || p->nnz == 0) return from_cuda(e);
     return from_cuda(launch_csr_backward_scatter(vdt, p->wG, p->w_tile_items, p->m, p->n, p->nnz, p->w_tile_row,
                                                  p->w_tile_nz, p->ro + 1, g, values, col_idx, dx, x_gathered, dvalues,
-                                                 stream));
+                                                 dvdt != LB_F32, stream));
 }
 
-lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, float *dvalues,
-                          cudaStream_t stream) {
+lb_status lb_spmv_dvalues(const lb_plan *p, const int *col_idx, const float *g, const float *x, void *dvalues,
+                          lb_dtype dvdt, cudaStream_t stream) {
     LB_NVTX_RANGE();
-    if (!p) return LB_ERR_INVALID_ARG;
+    if (!p || !dtype_ok(dvdt)) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return LB_OK;
-    if (!col_idx || !g || !x || !dvalues) return LB_ERR_INVALID_ARG;
+    if (!col_idx || !g || !x || !dvalues || !aligned(dvalues, value_bytes(dvdt))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(
-        launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, p->n, dvalues, stream));
+    return from_cuda(launch_dvalues(p->G, p->tile_items, p->tile_row, p->tile_nz, p->ro + 1, col_idx, g, x, p->n,
+                                    dvalues, dvdt, stream));
 }
 
-lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, float *dvalues,
-                                   cudaStream_t stream) {
+lb_status lb_spmv_dvalues_gathered(const lb_plan *p, const float *g, const float *x_gathered, void *dvalues,
+                                   lb_dtype dvdt, cudaStream_t stream) {
     LB_NVTX_RANGE();
-    if (!p) return LB_ERR_INVALID_ARG;
+    if (!p || !dtype_ok(dvdt)) return LB_ERR_INVALID_ARG;
     if (p->nnz == 0) return LB_OK;
-    if (!g || !x_gathered || !dvalues) return LB_ERR_INVALID_ARG;
+    if (!g || !x_gathered || !dvalues || !aligned(dvalues, value_bytes(dvdt))) return LB_ERR_INVALID_ARG;
     if (!on_device(p->device)) return LB_ERR_INVALID_ARG;
-    return from_cuda(launch_csr_backward(LB_F32, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row, p->w_tile_nz,
-                                         p->ro + 1, g, nullptr, nullptr, nullptr, x_gathered, dvalues, stream));
+    // The pass's value type only selects the gradient's storage here (no values are read).
+    return from_cuda(launch_csr_backward(dvdt, p->wG, p->w_tile_items, p->m, p->nnz, p->w_tile_row, p->w_tile_nz,
+                                         p->ro + 1, g, nullptr, nullptr, nullptr, x_gathered, dvalues, dvdt != LB_F32,
+                                         stream));
 }
 
 lb_status lb_spmm_planned(lb_plan *p, const int *col_idx, const void *values, lb_dtype vdt, int kc, const float *B,

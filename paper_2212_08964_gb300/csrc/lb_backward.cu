@@ -3,10 +3,29 @@
 // (dvalues from saved gathers, the scaled values for dx in CSC buckets, or their float
 // reductions into dx).
 #include <cstdint>
+#include <type_traits>
 
 #include "lb_warp.cuh"
 
 namespace lb {
+
+// A gradient value in the values' 16-bit type (round to nearest even), as its bits.
+template <typename T>
+__device__ __forceinline__ uint32_t narrow_bits(float v) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    else
+        return __half_as_ushort(__float2half_rn(v));
+}
+
+// Store one gradient value as T (FP32, or 16-bit rounded to nearest even).
+template <typename T>
+__device__ __forceinline__ void store_grad(void *base, long long k, float v) {
+    if constexpr (std::is_same<T, float>::value)
+        static_cast<float *>(base)[k] = v;
+    else
+        static_cast<unsigned short *>(base)[k] = static_cast<unsigned short>(narrow_bits<T>(v));
+}
 
 // ------------------------------------------------------------------------------------------
 // Per-nonzero maps over the forward merge-path partition.  Each tile stages its row ends;
@@ -14,13 +33,13 @@ namespace lb {
 // its IPT consecutive nonzeros (row ends are sorted), recording row ids in shared memory;
 // a second, coalesced pass reads the column indices and writes the outputs.
 
-template <int THREADS, int IPT, bool ROWID>
+template <int THREADS, int IPT, bool ROWID, typename DVT = float>
 __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__restrict__ tile_row,
                                                             const int *__restrict__ tile_nz,
                                                             const int *__restrict__ row_end,
                                                             const int *__restrict__ ci, const float *__restrict__ g,
                                                             const float *__restrict__ x, int n,
-                                                            float *__restrict__ dv, int *__restrict__ rowid) {
+                                                            void *__restrict__ dv, int *__restrict__ rowid) {
     constexpr int T = THREADS * IPT;
     __shared__ int s_re[T];
     __shared__ int s_row[T];
@@ -62,7 +81,7 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
                     rowid[k] = row;
                 else {
                     const int c = __ldg(ci + k);
-                    dv[k] = LB_IN_RANGE(c, n) ? __ldg(g + row) * __ldg(x + c) : 0.f;
+                    store_grad<DVT>(dv, k, LB_IN_RANGE(c, n) ? __ldg(g + row) * __ldg(x + c) : 0.f);
                 }
             }
         }
@@ -70,21 +89,21 @@ __global__ void __launch_bounds__(THREADS) tile_rows_kernel(int G, const int *__
     }
 }
 
-template <bool ROWID>
+template <bool ROWID, typename DVT = float>
 static cudaError_t launch_tile_rows(int G, int tile_items, const int *tile_row, const int *tile_nz,
                                     const int *row_end, const int *ci, const float *g, const float *x, int n,
-                                    float *dv, int *rowid, cudaStream_t st) {
+                                    void *dv, int *rowid, cudaStream_t st) {
     if (G <= 0) return cudaSuccess;
     int grid = G;
     const int cap = current_sm_count() * 6;
     if (grid > cap) grid = cap;
     // The staged row ends must fit: a tile holds at most tile_items rows.
     if (tile_items <= 1024)
-        tile_rows_kernel<256, 4, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
+        tile_rows_kernel<256, 4, ROWID, DVT><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
     else if (tile_items <= 2048)
-        tile_rows_kernel<256, 8, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
+        tile_rows_kernel<256, 8, ROWID, DVT><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
     else if (tile_items <= 4096)
-        tile_rows_kernel<256, 16, ROWID><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
+        tile_rows_kernel<256, 16, ROWID, DVT><<<grid, 256, 0, st>>>(G, tile_row, tile_nz, row_end, ci, g, x, n, dv, rowid);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -111,7 +130,8 @@ struct CsrBackwardArgs {
     const int *bucket_pos;  // null: pv in CSR order
     float *pv;              // null: no scaled values
     const float *xg;        // saved gathers (with dv)
-    float *dv;              // null: no values gradient
+    void *dv;               // null: no values gradient; FP32, or the values' type when dv_narrow
+    int dv_narrow;          // dv holds the values' 16-bit type (rounded to nearest even)
     const int *ci;          // SCATTER: column indices
     float *dx;              // SCATTER: dx accumulated by float reductions
     int vec_v, vec_xg, vec_dv, vec_ci;  // the arrays' bases are 32-byte (16-bit values: 16-byte) aligned
@@ -267,13 +287,35 @@ __global__ void __launch_bounds__(256) csr_backward_kernel(const CsrBackwardArgs
             float d[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) d[q] = gq[q] * xv[q];
-            if (vm == (1u << IPT) - 1u && a.vec_dv) {
+            if (sizeof(V) == 2 && a.dv_narrow) {  // the values' type: 16 bytes per lane
+                unsigned short *dvn = static_cast<unsigned short *>(a.dv);
+                if (vm == (1u << IPT) - 1u && a.vec_dv) {
 #pragma unroll
-                for (int h = 0; h < IPT; h += 8) st_stream8(a.dv + e0 + h, pol, d + h);
+                    for (int h = 0; h < IPT; h += 8) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            w[i] = narrow_bits<V>(d[h + 2 * i]) | (narrow_bits<V>(d[h + 2 * i + 1]) << 16);
+                        asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.b32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(
+                                         dvn + e0 + h),
+                                     "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "l"(pol)
+                                     : "memory");
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if ((vm >> q) & 1u) dvn[e0 + q] = static_cast<unsigned short>(narrow_bits<V>(d[q]));
+                }
             } else {
+                float *dvf = static_cast<float *>(a.dv);
+                if (vm == (1u << IPT) - 1u && a.vec_dv) {
 #pragma unroll
-                for (int q = 0; q < IPT; ++q)
-                    if ((vm >> q) & 1u) __stcs(a.dv + e0 + q, d[q]);
+                    for (int h = 0; h < IPT; h += 8) st_stream8(dvf + e0 + h, pol, d + h);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q)
+                        if ((vm >> q) & 1u) __stcs(dvf + e0 + q, d[q]);
+                }
             }
         }
         if (SCATTER) {
@@ -312,7 +354,7 @@ static cudaError_t launch_csr_backward_ipt(CsrBackwardArgs a, cudaStream_t strea
     const size_t vb = (sizeof(V) == 4) ? 31u : 15u;
     a.vec_v = (reinterpret_cast<uintptr_t>(a.values) & vb) == 0;
     a.vec_xg = (reinterpret_cast<uintptr_t>(a.xg) & 31u) == 0;
-    a.vec_dv = (reinterpret_cast<uintptr_t>(a.dv) & 31u) == 0;
+    a.vec_dv = (reinterpret_cast<uintptr_t>(a.dv) & (a.dv_narrow ? 15u : 31u)) == 0;
     a.vec_ci = (reinterpret_cast<uintptr_t>(a.ci) & 31u) == 0;
     kern<<<static_cast<int>(grid), threads, smem, stream>>>(a);
     return cudaGetLastError();
@@ -328,13 +370,15 @@ static cudaError_t launch_csr_backward_t(CsrBackwardArgs a, int tile_items, cuda
 
 cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz, const int *tile_row,
                                 const int *tile_nz, const int *row_end, const float *g, const void *values,
-                                const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream) {
+                                const int *bucket_pos, float *pv, const float *xg, void *dv, bool dv_narrow,
+                                cudaStream_t stream) {
     if (num_tiles <= 0) return cudaSuccess;
     if ((pv != nullptr && values == nullptr) || (dv != nullptr && xg == nullptr)) return cudaErrorInvalidValue;
+    if (dv_narrow && vdt == LB_F32) return cudaErrorInvalidValue;
     CsrBackwardArgs a{};
     a.G = num_tiles, a.m = m, a.nnz = nnz;
     a.tile_row = tile_row, a.tile_nz = tile_nz, a.row_end = row_end, a.g = g, a.values = values;
-    a.bucket_pos = bucket_pos, a.pv = pv, a.xg = xg, a.dv = dv;
+    a.bucket_pos = bucket_pos, a.pv = pv, a.xg = xg, a.dv = dv, a.dv_narrow = dv_narrow ? 1 : 0;
     switch (vdt) {
         case LB_F32:
             return launch_csr_backward_t<float, false>(a, tile_items, stream);
@@ -349,14 +393,16 @@ cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int tile_items, int
 cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int n, int nnz,
                                         const int *tile_row,
                                         const int *tile_nz, const int *row_end, const float *g, const void *values,
-                                        const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream) {
+                                        const int *ci, float *dx, const float *xg, void *dv, bool dv_narrow,
+                                        cudaStream_t stream) {
     if (num_tiles <= 0) return cudaSuccess;
     if (values == nullptr || ci == nullptr || dx == nullptr || (dv != nullptr && xg == nullptr))
         return cudaErrorInvalidValue;
+    if (dv_narrow && vdt == LB_F32) return cudaErrorInvalidValue;
     CsrBackwardArgs a{};
     a.G = num_tiles, a.m = m, a.nnz = nnz;
     a.tile_row = tile_row, a.tile_nz = tile_nz, a.row_end = row_end, a.g = g, a.values = values;
-    a.xg = xg, a.dv = dv, a.ci = ci, a.dx = dx, a.n = n;
+    a.xg = xg, a.dv = dv, a.dv_narrow = dv_narrow ? 1 : 0, a.ci = ci, a.dx = dx, a.n = n;
     switch (vdt) {
         case LB_F32:
             return launch_csr_backward_t<float, true>(a, tile_items, stream);
@@ -369,10 +415,20 @@ cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_it
 }
 
 cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, int n, float *dv,
-                           cudaStream_t stream) {
-    return launch_tile_rows<false>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, n, dv, nullptr,
-                                   stream);
+                           const int *row_end, const int *ci, const float *g, const float *x, int n, void *dv,
+                           lb_dtype dvdt, cudaStream_t stream) {
+    switch (dvdt) {
+        case LB_F32:
+            return launch_tile_rows<false, float>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, n, dv,
+                                                  nullptr, stream);
+        case LB_BF16:
+            return launch_tile_rows<false, __nv_bfloat16>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, n,
+                                                          dv, nullptr, stream);
+        case LB_F16:
+            return launch_tile_rows<false, __half>(num_tiles, tile_items, tile_row, tile_nz, row_end, ci, g, x, n, dv,
+                                                   nullptr, stream);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,

@@ -135,10 +135,11 @@ cudaError_t launch_partition(int m, long long nnz, const int *offsets, int tile_
 cudaError_t launch_mapped(lb_schedule s, const lb_tuning &t, lb_dtype vdt, int m, int n, int nnz, const int *ro,
                           const int *ci, const void *v, const float *x, float *y, cudaStream_t stream);
 
-// dvalues over the forward block tiles, gathering x: dv[k] = g[row(k)] * x[ci[k]].
+// dvalues over the forward block tiles, gathering x: dv[k] = g[row(k)] * x[ci[k]], stored as
+// dvdt (FP32, or BF16/FP16 rounded to nearest even).
 cudaError_t launch_dvalues(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
-                           const int *row_end, const int *ci, const float *g, const float *x, int n, float *dv,
-                           cudaStream_t stream);
+                           const int *row_end, const int *ci, const float *g, const float *x, int n, void *dv,
+                           lb_dtype dvdt, cudaStream_t stream);
 
 // Stable CSR -> CSC transpose (deterministic LSD radix sort by column).
 struct TransposeOut {
@@ -160,10 +161,12 @@ cudaError_t build_value_buckets(int nnz, int shift, const int *perm, int *bucket
 // One streaming pass over the nonzeros in CSR order, over the forward's warp tiles (merge-path
 // tiles of merge_tile_items(8) or (16) items): the scaled values pv[pos(k)] = values[k] *
 // g[row(k)] with pos = bucket_pos (identity when null), when pv is given, and
-// dv[k] = g[row(k)] * xg[k] when xg and dv are given.
+// dv[k] = g[row(k)] * xg[k] when xg and dv are given (FP32, or the 16-bit values' type vdt
+// when dv_narrow).
 cudaError_t launch_csr_backward(lb_dtype vdt, int num_tiles, int tile_items, int m, int nnz, const int *tile_row,
                                 const int *tile_nz, const int *row_end, const float *g, const void *values,
-                                const int *bucket_pos, float *pv, const float *xg, float *dv, cudaStream_t stream);
+                                const int *bucket_pos, float *pv, const float *xg, void *dv, bool dv_narrow,
+                                cudaStream_t stream);
 
 // rowid[k] = the row of nonzero k, over the forward block tiles.
 cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_row, const int *tile_nz,
@@ -173,7 +176,8 @@ cudaError_t launch_tile_row_ids(int num_tiles, int tile_items, const int *tile_r
 cudaError_t launch_csr_backward_scatter(lb_dtype vdt, int num_tiles, int tile_items, int m, int n, int nnz,
                                         const int *tile_row,
                                         const int *tile_nz, const int *row_end, const float *g, const void *values,
-                                        const int *ci, float *dx, const float *xg, float *dv, cudaStream_t stream);
+                                        const int *ci, float *dx, const float *xg, void *dv, bool dv_narrow,
+                                        cudaStream_t stream);
 
 // Batched-plan helpers.
 // Thread-mapped SpMV over a batch's block-diagonal matrix (rows longer than a few nonzeros

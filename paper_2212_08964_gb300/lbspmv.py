@@ -117,11 +117,11 @@ def _declare(lib):
         "lb_plan_build_transpose": [_P, _P, _P],
         "lb_plan_transpose": [_P, _P, _P, _P],
         "lb_spmv_t": [_P, _P, _I, _P, _P, _P],
-        "lb_spmv_dvalues": [_P, _P, _P, _P, _P, _P],
+        "lb_spmv_dvalues": [_P, _P, _P, _P, _P, _I, _P],
         "lb_spmv_planned_save": [_P, _P, _P, _I, _P, _P, _P, _P],
-        "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _P],
-        "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _P],
-        "lb_spmv_backward_scatter": [_P, _P, _P, _I, _P, _P, _P, _P, _P],
+        "lb_spmv_dvalues_gathered": [_P, _P, _P, _P, _I, _P],
+        "lb_spmv_backward": [_P, _P, _I, _P, _P, _P, _P, _I, _P],
+        "lb_spmv_backward_scatter": [_P, _P, _P, _I, _P, _P, _P, _P, _I, _P],
         "lb_spmm_planned": [_P, _P, _P, _I, _I, _P, _P, _P],
         "lb_coo_row_offsets": [_I, _I, _P, _P, _P, _P],
         "lb_calibrate": [ctypes.POINTER(Calibration), _P],
@@ -210,6 +210,13 @@ def _vdt(values: torch.Tensor) -> int:
         return _DTYPES[values.dtype]
     except KeyError:
         raise TypeError(f"values must be float32, bfloat16 or float16, got {values.dtype}") from None
+
+
+def _dv_type(dvalues: torch.Tensor, values: torch.Tensor) -> int:
+    """The values gradient's storage: float32, or the values' own 16-bit type."""
+    if dvalues.dtype != torch.float32 and dvalues.dtype != values.dtype:
+        raise TypeError(f"dvalues must be float32 or the values' type {values.dtype}, got {dvalues.dtype}")
+    return _vdt(dvalues)
 
 
 def _tuning(threads=0, items_per_thread=0, group_size=0):
@@ -383,31 +390,35 @@ class Plan:
         _check(_lib.lb_spmv_t(self._h, _ptr(values), _vdt(values), _ptr(g), _ptr(dx), _stream(stream)), "lb_spmv_t")
         return dx
 
-    def dvalues(self, col_idx, g, x, out=None, stream=None) -> torch.Tensor:
+    def dvalues(self, col_idx, g, x, out=None, stream=None, dtype=torch.float32) -> torch.Tensor:
+        """dvalues[k] = g[row(k)] * x[col_idx[k]] gathering x; stored in ``out``'s type (else
+        ``dtype``): float32, or bfloat16/float16 rounded to nearest even."""
         _need(col_idx, torch.int32, "col_idx", self.nnz)
         _need(g, torch.float32, "g", self.m)
         _need(x, torch.float32, "x", self.n)
-        dv = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if out is None else out
-        _need(dv, torch.float32, "dvalues", self.nnz)
-        _check(_lib.lb_spmv_dvalues(self._h, _ptr(col_idx), _ptr(g), _ptr(x), _ptr(dv), _stream(stream)), "lb_spmv_dvalues")
+        dv = torch.empty(self.nnz, dtype=dtype, device=g.device) if out is None else out
+        _need(dv, None, "dvalues", self.nnz)
+        _check(_lib.lb_spmv_dvalues(self._h, _ptr(col_idx), _ptr(g), _ptr(x), _ptr(dv), _vdt(dv), _stream(stream)),
+               "lb_spmv_dvalues")
         return dv
 
-    def backward(self, values, g, x_gathered, dx=None, dvalues=None, stream=None):
+    def backward(self, values, g, x_gathered, dx=None, dvalues=None, stream=None, dvalues_dtype=torch.float32):
         """(dx, dvalues) = (A^T g, g[row] * x_gathered) in two passes (lb_spmv_backward);
-        needs ``build_transpose`` and x gathers saved by ``spmv(save_gathered=...)``."""
+        needs ``build_transpose`` and x gathers saved by ``spmv(save_gathered=...)``.  dvalues
+        is float32 or the values' 16-bit type (``dvalues``' own type, else ``dvalues_dtype``)."""
         _need(values, None, "values", self.nnz)
         _need(g, torch.float32, "g", self.m)
         _need(x_gathered, torch.float32, "x_gathered", self.nnz)
         dx = torch.empty(self.n, dtype=torch.float32, device=g.device) if dx is None else dx
-        dvalues = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if dvalues is None else dvalues
+        dvalues = torch.empty(self.nnz, dtype=dvalues_dtype, device=g.device) if dvalues is None else dvalues
         _need(dx, torch.float32, "dx", self.n)
-        _need(dvalues, torch.float32, "dvalues", self.nnz)
+        _need(dvalues, None, "dvalues", self.nnz)
         _check(_lib.lb_spmv_backward(self._h, _ptr(values), _vdt(values), _ptr(g), _ptr(x_gathered), _ptr(dx),
-                                     _ptr(dvalues), _stream(stream)), "lb_spmv_backward")
+                                     _ptr(dvalues), _dv_type(dvalues, values), _stream(stream)), "lb_spmv_backward")
         return dx, dvalues
 
     def backward_scatter(self, col_idx, values, g, x_gathered=None, dx=None, dvalues=None, want_dvalues=True,
-                         stream=None):
+                         stream=None, dvalues_dtype=torch.float32):
         """(dx, dvalues) in one CSR-order pass without a CSC view (lb_spmv_backward_scatter):
         dx by float reductions into dx[col] (within tolerance, not bit-reproducible), dvalues
         as ``backward`` (bit-exact; needs ``x_gathered``).  dvalues is None when not wanted."""
@@ -418,23 +429,26 @@ class Plan:
         _need(dx, torch.float32, "dx", self.n)
         if want_dvalues:
             _need(x_gathered, torch.float32, "x_gathered", self.nnz)
-            dvalues = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if dvalues is None else dvalues
-            _need(dvalues, torch.float32, "dvalues", self.nnz)
+            dvalues = torch.empty(self.nnz, dtype=dvalues_dtype, device=g.device) if dvalues is None else dvalues
+            _need(dvalues, None, "dvalues", self.nnz)
         else:
             dvalues = None
         _check(_lib.lb_spmv_backward_scatter(self._h, _ptr(col_idx), _ptr(values), _vdt(values), _ptr(g),
                                              _ptr(x_gathered) if x_gathered is not None else None, _ptr(dx),
-                                             _ptr(dvalues) if dvalues is not None else None, _stream(stream)),
+                                             _ptr(dvalues) if dvalues is not None else None,
+                                             _dv_type(dvalues, values) if dvalues is not None else 0,
+                                             _stream(stream)),
                "lb_spmv_backward_scatter")
         return dx, dvalues
 
-    def dvalues_gathered(self, g, x_gathered, out=None, stream=None) -> torch.Tensor:
-        """dvalues[k] = g[row(k)] * x_gathered[k] (x gathers saved by ``spmv(save_gathered=...)``)."""
+    def dvalues_gathered(self, g, x_gathered, out=None, stream=None, dtype=torch.float32) -> torch.Tensor:
+        """dvalues[k] = g[row(k)] * x_gathered[k] (x gathers saved by ``spmv(save_gathered=...)``),
+        stored in ``out``'s type (else ``dtype``), as ``dvalues``."""
         _need(g, torch.float32, "g", self.m)
         _need(x_gathered, torch.float32, "x_gathered", self.nnz)
-        dv = torch.empty(self.nnz, dtype=torch.float32, device=g.device) if out is None else out
-        _need(dv, torch.float32, "dvalues", self.nnz)
-        _check(_lib.lb_spmv_dvalues_gathered(self._h, _ptr(g), _ptr(x_gathered), _ptr(dv), _stream(stream)),
+        dv = torch.empty(self.nnz, dtype=dtype, device=g.device) if out is None else out
+        _need(dv, None, "dvalues", self.nnz)
+        _check(_lib.lb_spmv_dvalues_gathered(self._h, _ptr(g), _ptr(x_gathered), _ptr(dv), _vdt(dv), _stream(stream)),
                "lb_spmv_dvalues_gathered")
         return dv
 
@@ -569,25 +583,25 @@ class SpMV(torch.autograd.Function):
         plan = ctx.plan
         g = g.contiguous().float()
         dvals = dx = None
+        # The values gradient takes the values' type, rounded in the library's kernels.
+        dvt = values.dtype
         if not ctx.deterministic and ctx.needs_input_grad[1]:
             want_dv = ctx.needs_input_grad[0] and xg is not None
-            dx, dvals = plan.backward_scatter(col_idx, values.detach(), g, xg, want_dvalues=want_dv)
+            dx, dvals = plan.backward_scatter(col_idx, values.detach(), g, xg, want_dvalues=want_dv,
+                                              dvalues_dtype=dvt)
             if ctx.needs_input_grad[0] and dvals is None:
-                dvals = plan.dvalues(col_idx, g, x.detach())
-            if dvals is not None and values.dtype != torch.float32:
-                dvals = dvals.to(values.dtype)
+                dvals = plan.dvalues(col_idx, g, x.detach(), dtype=dvt)
             return dvals, dx, None, None, None
         if ctx.needs_input_grad[1] and not plan.has_transpose:
             plan.build_transpose(col_idx)
         if ctx.needs_input_grad[0] and ctx.needs_input_grad[1] and xg is not None:
-            dx, dvals = plan.backward(values.detach(), g, xg)  # both in two passes
+            dx, dvals = plan.backward(values.detach(), g, xg, dvalues_dtype=dvt)  # both in two passes
         else:
             if ctx.needs_input_grad[0]:
-                dvals = plan.dvalues(col_idx, g, x.detach()) if xg is None else plan.dvalues_gathered(g, xg)
+                dvals = (plan.dvalues(col_idx, g, x.detach(), dtype=dvt) if xg is None
+                         else plan.dvalues_gathered(g, xg, dtype=dvt))
             if ctx.needs_input_grad[1]:
                 dx = plan.spmv_t(values.detach(), g)
-        if dvals is not None and values.dtype != torch.float32:
-            dvals = dvals.to(values.dtype)
         return dvals, dx, None, None, None
 
 

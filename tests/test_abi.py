@@ -79,7 +79,12 @@ def test_host_side_argument_rejection(lib):
     assert lib.lb_batched_plan_create(1, one, one, one, ctypes.c_void_p(16), 2, None, None, ctypes.byref(out)) == -3
     assert lib.lb_spmv_planned(None, None, None, 0, None, None, None) == -1
     assert lib.lb_spmv_t(None, None, 0, None, None, None) == -1
-    assert lib.lb_spmv_dvalues(None, None, None, None, None, None) == -1
+    assert lib.lb_spmv_dvalues(None, None, None, None, None, 0, None) == -1
+    # dvalues types: FP32 or the values' 16-bit type only (a fake plan pointer, never read:
+    # the type check comes first).
+    fake = ctypes.c_void_p(256)
+    assert lib.lb_spmv_dvalues(fake, None, None, None, None, 7, None) == -1
+    assert lib.lb_spmv_dvalues_gathered(fake, None, None, None, 7, None) == -1
     assert lib.lb_spmv_batched(None, None, None, 0, None, None, None) == -1
     assert lib.lb_validate_csr(-1, 0, 0, None, None, 0, None, None) == -1
     assert lib.lb_device_error(None, 0) == -1

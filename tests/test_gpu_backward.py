@@ -357,3 +357,60 @@ def test_training_step_in_a_cuda_graph(lb, orc):
     assert torch.equal(y, ref[0]) and torch.equal(dx, ref[1]) and torch.equal(dv, ref[2])
     check_bound(dx.cpu().numpy(), orc.spmv_t(a.row_offsets, a.col_idx, a.values, vec(a.m, 222), a.n),
                 orc.col_absdot(a.row_offsets, a.col_idx, a.values, vec(a.m, 222), a.n), TOL32, "columns")
+
+
+def _dv16(ref_f64, dtype):
+    """The oracle's dvalues as the library stores them in a 16-bit type: the exact product of
+    two FP32 numbers rounded to FP32 (what FP32 arithmetic gives), then to nearest even."""
+    return torch.from_numpy(ref_f64.astype(np.float32)).to(dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("name", ["powerlaw_4k", "skew", "worked"])
+def test_values_gradient_in_the_values_type(lb, orc, name, dtype):
+    """dvalues stored in the 16-bit values' own type by every entry point that forms it (the
+    two-pass backward, the scattered backward, from saved gathers and gathering x), bit-exact
+    against the oracle's product rounded the same way; another 16-bit type is refused."""
+    a = _cases()[name]
+    plan, ci, v = _plan_with_t(lb, a, dtype=dtype)
+    x = vec(a.n, 231)
+    g = vec(a.m, 232)
+    xg = torch.empty(a.nnz, device="cuda")
+    plan.spmv(ci, v, dev(x), save_gathered=xg)
+    ref = _dv16(orc.dvalues(a.row_offsets, a.col_idx, g, x), dtype)
+    dx32, dv32 = plan.backward(v, dev(g), xg)
+    dx, dv = plan.backward(v, dev(g), xg, dvalues_dtype=dtype)
+    _, dvs = plan.backward_scatter(ci, v, dev(g), xg, dvalues_dtype=dtype)
+    dvg = plan.dvalues_gathered(dev(g), xg, dtype=dtype)
+    dvx = plan.dvalues(ci, dev(g), dev(x), dtype=dtype)
+    torch.cuda.synchronize()
+    assert torch.equal(dx, dx32)
+    for got in (dv, dvs, dvg, dvx):
+        assert got.dtype == dtype and torch.equal(got.cpu(), ref)
+    assert torch.equal(dv.cpu(), dv32.cpu().to(dtype))
+    with pytest.raises(TypeError):
+        plan.backward(v, dev(g), xg, dvalues_dtype=torch.float16 if dtype == torch.bfloat16 else torch.bfloat16)
+    # A 16-bit gradient one element off a 16-byte boundary takes the element-wise stores.
+    buf = torch.full((a.nnz + 1,), float("nan"), dtype=dtype, device="cuda")
+    plan.backward(v, dev(g), xg, dvalues=buf[1:])
+    torch.cuda.synchronize()
+    assert torch.equal(buf[1:].cpu(), ref) and torch.isnan(buf[:1]).all()
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("deterministic", [True, False])
+def test_autograd_values_gradient_16bit(lb, orc, dtype, deterministic):
+    """With 16-bit values, the autograd function's values gradient arrives in that type from
+    the library's kernels, equal to the oracle's product rounded to nearest even."""
+    a = workload("powerlaw_4k")
+    ro, ci, v = to_dev(a, dtype)
+    plan = lb.Plan(ro, a.n, a.nnz, schedule="merge_path")
+    x = vec(a.n, 233)
+    g = vec(a.m, 234)
+    vt = v.clone().requires_grad_(True)
+    xt = dev(x).requires_grad_(True)
+    y = lb.spmv_autograd(plan, ci, vt, xt, deterministic=deterministic)
+    y.backward(dev(g))
+    torch.cuda.synchronize()
+    assert vt.grad.dtype == dtype
+    assert torch.equal(vt.grad.cpu(), _dv16(orc.dvalues(a.row_offsets, a.col_idx, g, x), dtype))
