@@ -48,12 +48,18 @@ __global__ void sssp_init_kernel(int n, int source, float *dist, int *stamp, int
     if (blockIdx.x == 0 && threadIdx.x == 0) frontier[0] = source;
 }
 
+// deg[i] = out-degree of frontier vertex i, deg[fsize] = 0 (the scan's last entry becomes the
+// edge count), and the next frontier's counter cleared for the relaxation that follows.
 __global__ void frontier_degrees_kernel(int fsize, const int *__restrict__ frontier, const int *__restrict__ ro,
-                                        int *__restrict__ deg) {
+                                        int *__restrict__ deg, int *__restrict__ next_count) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < fsize;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
         const int u = __ldg(frontier + i);
         deg[i] = __ldg(ro + u + 1) - __ldg(ro + u);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        deg[fsize] = 0;
+        *next_count = 0;
     }
 }
 
@@ -185,12 +191,10 @@ cudaError_t run_sssp(int n, int nnz, const int *ro, const int *ci, const float *
         // Near iterations: relax the frontier until no distance below the split drops.
         while (e == cudaSuccess && fsize > 0 && tick < tick_limit) {
             ++tick;
-            frontier_degrees_kernel<<<blocks(fsize), kGraphThreads, 0, st>>>(fsize, f_cur, ro, pre);
+            frontier_degrees_kernel<<<blocks(fsize), kGraphThreads, 0, st>>>(fsize, f_cur, ro, pre, d_cnt);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
-            // pre[fsize] = 0 then scan fsize + 1 entries: pre[fsize] is the frontier's edge count.
-            if ((e = cudaMemsetAsync(pre + fsize, 0, sizeof(int), st)) != cudaSuccess) break;
+            // Scan fsize + 1 entries (pre[fsize] = 0): pre[fsize] is the frontier's edge count.
             if ((e = exclusive_scan(pre, pre, static_cast<long long>(fsize) + 1, sums, st)) != cudaSuccess) break;
-            if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(int), st)) != cudaSuccess) break;
             // The edge count stays on the device; the relaxation reads it and strides over it.
             relax_kernel<<<sms * 16, kGraphThreads, 0, st>>>(n, fsize, tick, split, f_cur, pre, ro, ci, w, dist, stamp,
                                                              far, f_next, d_cnt);

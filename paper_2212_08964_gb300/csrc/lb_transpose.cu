@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in,
     }
     if (lane == 31) s_w[warp] = incl;
     __syncthreads();
-    int run = sums[blockIdx.x] + incl - tot;
+    int run = (sums != nullptr ? sums[blockIdx.x] : 0) + incl - tot;  // null: a single chunk
     for (int w = 0; w < warp; ++w) run += s_w[w];
 #pragma unroll
     for (int u = 0; u < kScanItems; ++u) {
@@ -106,6 +106,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in,
 cudaError_t exclusive_scan(const int *in, int *out, long long n, int *sums, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int nb = static_cast<int>((n + kScanChunk - 1) / kScanChunk);
+    if (nb == 1) {  // one chunk: one block scans it, with no chunk sums
+        scan_apply_kernel<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        return cudaGetLastError();
+    }
     scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, sums);
     scan_sums_kernel<<<1, 1024, 0, st>>>(sums, nb);
     scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n, sums);
